@@ -1,0 +1,287 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these tests retypes an oracle formula: each compares the oracle with an
+independent value -- a closed form, a brute-force state-vector computation, a
+linear-algebra identity, a symmetry, or a finite difference.
+"""
+import numpy as np
+import pytest
+import torch
+
+import ipeps_inputs as I
+from oracle import ctmrg as C
+from oracle import energy as En
+from oracle import statevector as SV
+from oracle.svd import svd as osvd
+
+H = I.heisenberg_bond()
+HR = I.heisenberg_bond_rotated()
+
+
+def E_split(A, chi, sweeps, h, hd=None):
+    env = C.split_ctmrg(A, chi=chi, sweeps=sweeps)
+    return float(En.energy_per_site(A, env, h, hd))
+
+
+# ------------------------------------------------------- closed forms (D = 1)
+@pytest.mark.parametrize("D", [1, 2])
+def test_product_state_rotated_one_site_is_minus_half(D):
+    """Any real product state in the sublattice-rotated frame: -1/4 per bond,
+    two bonds per site -> -1/2 (Bloch vector of a real state has unit length)."""
+    rng = np.random.default_rng(0)
+    phi = rng.standard_normal((1, 1, 2))
+    A = I.product_state_cell(phi, D=D)
+    assert abs(E_split(A, chi=8, sweeps=2, h=HR) + 0.5) < 1e-12
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_product_state_2x2_closed_form(D):
+    """Real product state, 2x2 cell, J1-J2: every bond factorises."""
+    rng = np.random.default_rng(1)
+    phis = rng.standard_normal((2, 2, 2))
+    A = I.product_state_cell(phis, D=D)
+    if D > 1:
+        A = I.gauge_transform_cell(A, seed=2)
+    ref = SV.product_energy(phis, H, 0.5 * H)
+    assert abs(E_split(A, chi=12, sweeps=2, h=H, hd=0.5 * H) - ref) < 1e-11
+
+
+def test_neel_closed_form():
+    """Neel in a 2x2 cell: -1/4 per NN bond, +1/4 per diagonal -> -1/2 + J2/2."""
+    phis = np.zeros((2, 2, 2))
+    phis[0, 0, 0] = phis[1, 1, 0] = 1.0
+    phis[0, 1, 1] = phis[1, 0, 1] = 1.0
+    A = I.product_state_cell(phis, D=2)
+    for J2 in (0.0, 0.5):
+        E = E_split(A, chi=4, sweeps=2, h=H, hd=J2 * H)
+        assert abs(E - (-0.5 + 0.5 * J2)) < 1e-12
+
+
+def test_singlet_dimers():
+    """Singlets on horizontal bonds: -3/4 per singlet, 0 elsewhere -> -3/8 per site."""
+    A = I.dimer_cell(D=2)
+    assert abs(E_split(A, chi=8, sweeps=3, h=H, hd=0.5 * H) + 0.375) < 1e-12
+
+
+# ------------------------------------------------ brute-force cluster states
+@pytest.mark.parametrize("vertical", [False, True])
+@pytest.mark.parametrize("D", [2, 3])
+def test_generic_dimer_states_exact(vertical, D):
+    """Product of generic two-site states (gauge-scrambled bonds, so every leg is
+    dense): CTMRG must reproduce the state-vector energy exactly."""
+    rng = np.random.default_rng(10 + D + 3 * vertical)
+    psis = rng.standard_normal((2, 2, 2))
+    A = I.gauge_transform_cell(I.dimer_pairs_cell(psis, D=D, vertical=vertical), seed=3)
+    ref = SV.dimer_pairs_energy(psis, H, 0.5 * H, vertical=vertical)
+    assert abs(E_split(A, chi=16, sweeps=3, h=H, hd=0.5 * H) - ref) < 1e-10
+
+
+def test_plaquette_patch_bonds_exact():
+    """Product of generic 4-site plaquettes: every bond of the patch that holds a
+    whole plaquette (anchor (0,0)) equals the state-vector value, including both
+    diagonals; bonds between plaquettes factorise."""
+    rng = np.random.default_rng(4)
+    psi = rng.standard_normal((2, 2, 2, 2))
+    psi /= np.linalg.norm(psi)
+    A = I.gauge_transform_cell(I.plaquette_cell(psi, D=4), seed=5, scale=0.2)
+    env = C.split_ctmrg(A, chi=24, sweeps=3)
+    _, bonds = En.energy_per_site(A, env, H, H, return_bonds=True)
+    rdm1, rdm2 = SV._cluster_state_pairs(psi)
+    v = bonds[(0, 0)]
+    pairs = {"top": (0, 1), "bottom": (2, 3), "left": (0, 2), "right": (1, 3),
+             "diag1": (0, 3), "diag2": (1, 2)}
+    for k, (i, j) in pairs.items():
+        assert abs(float(v[k]) - SV._two_site_value(rdm2[(i, j)], H)) < 1e-10, k
+    # patch (1,1): all four sites in different plaquettes -> products
+    w = bonds[(1, 1)]
+    prod = lambda i, j: SV._two_site_value(np.einsum("sT,vU->svTU", rdm1[i], rdm1[j]), H)
+    assert abs(float(w["top"]) - prod(3, 2)) < 1e-10
+    assert abs(float(w["left"]) - prod(3, 1)) < 1e-10
+    assert abs(float(w["diag1"]) - prod(3, 0)) < 1e-10
+
+
+# ------------------------------------------------------ projector identities
+def _env_after(A, chi, sweeps):
+    Ac = C.as_cell(A)
+    return Ac, C.split_ctmrg(Ac, chi=chi, sweeps=sweeps)
+
+
+@pytest.mark.parametrize("chi", [6, 40])
+def test_projector_identities(chi):
+    """For every colour: P_up P_dn = 1 on the kept space, P_dn P_up idempotent,
+    and rho^B P_dn P_up rho^T equals the best rank-chi approximation of M
+    (Eckart-Young: the residual is the norm of the discarded singular values)."""
+    A = I.random_cell(2, 2, 2, 2, seed=7)
+    Ac, env = _env_after(A, chi, 1)
+    rec = {}
+    E, a, K, Pg, Py, Pt, Pr, E2, a2 = C.split_column_projectors(Ac, env, 0, chi, record=rec)
+    rhos = {
+        "green": (C.green_rhoT(E[0], a[0]), C.green_rhoB(E[1], a[1])),
+        "yellow": (C.yellow_rhoT(E[0], a[0]), C.yellow_rhoB(E[0], a[0])),
+        "teal": (C.teal_rhoT(E[0], a[0], K[0], E2[0], a2[0]),
+                 C.teal_rhoB(E[1], a[1], K[1], E2[1], a2[1])),
+        "red": (C.red_rhoT(E[0], K[0], E2[0], a2[0]), C.red_rhoB(E[0], a[0], K[0], E2[0], a2[0])),
+    }
+    for colour, (rT, rB) in rhos.items():
+        up, dn, s = rec[colour][0]
+        k = up.shape[0]
+        M = rB @ rT
+        sv = torch.linalg.svdvals(M)
+        kept = int((s > 1e-8 * s[0]).sum())
+        I_k = (up @ dn)[:kept, :kept]
+        # rounding error of entry (i,j) scales like eps * s_max / sqrt(s_i s_j)
+        cond = float(s[0]) / torch.sqrt(s[:kept, None] * s[None, :kept])
+        err = (I_k - torch.eye(kept, dtype=I_k.dtype)).abs()
+        assert bool((err <= 1e-12 * cond + 1e-12).all()), colour
+        # idempotence on the well-conditioned part of the kept space
+        kw = int((s > 1e-6 * s[0]).sum())
+        Pw = dn[:, :kw] @ up[:kw]
+        assert torch.allclose(Pw @ Pw, Pw, atol=1e-9 * max(1.0, float(Pw.abs().max()))), colour
+        P = dn @ up
+        resid = torch.linalg.norm(rB @ P @ rT - M)
+        expect = torch.sqrt((sv[k:] ** 2).sum())
+        assert abs(float(resid) - float(expect)) < 1e-8 * float(sv[0]), colour
+
+
+def test_split_edges_contract_to_conventional():
+    """Contracting T^ket T^bra over the interlayer bond gives the conventional
+    double-layer edge when the split keeps the full rank (chi >= D^3)."""
+    A = C.as_cell(I.random_cell(2, 2, 2, 2, seed=9))
+    split = C.fuse(C.initial_env(A, chi=64, split=True))
+    conv = C.initial_env(A, chi=64, split=False)
+    for x in range(2):
+        for y in range(2):
+            for key in ("T1", "T2", "T3", "T4"):
+                assert torch.allclose(split[x][y][key], conv[x][y][key], atol=1e-12)
+
+
+# ------------------------------------------------------ symmetry / agreement
+def _ising_peps(beta):
+    """Tensor whose squared amplitude is the classical 2D Ising weight
+    exp(beta * sum_<ij> s_i s_j): A = prod over legs of Q[s, leg], Q Q^T = W."""
+    W = np.exp(0.5 * beta * np.array([[1.0, -1.0], [-1.0, 1.0]]))
+    w, V = np.linalg.eigh(W)
+    Q = V * np.sqrt(w)
+    return np.einsum("su,sl,sd,sr->suldr", Q, Q, Q, Q)[None, None]
+
+
+def _onsager_nn(beta):
+    """Nearest-neighbour <s_i s_j> of the square-lattice Ising model (Onsager):
+    u = -coth(2b) [1 + (2/pi)(2 tanh^2(2b) - 1) K(k)], k = 2 sinh(2b)/cosh^2(2b)."""
+    from scipy.special import ellipk
+    k = 2 * np.sinh(2 * beta) / np.cosh(2 * beta) ** 2
+    return 0.5 / np.tanh(2 * beta) * (1 + (2 / np.pi) * (2 * np.tanh(2 * beta) ** 2 - 1) * ellipk(k * k))
+
+
+@pytest.mark.parametrize("split", [True, False])
+def test_ising_peps_matches_onsager(split):
+    """<Z_i Z_j> of the Ising PEPS equals Onsager's exact value; the tensor is
+    gauge-scrambled so that no leg permutation or corner transpose can hide."""
+    beta = 0.3
+    A = C.as_cell(I.gauge_transform_cell(_ising_peps(beta), seed=3, scale=0.4))
+    ZZ = np.kron(np.diag([1.0, -1.0]), np.diag([1.0, -1.0]))
+    env = C.split_ctmrg(A, 12, 25) if split else C.conv_ctmrg(A, 12, 25)
+    _, bonds = En.energy_per_site(A, env, ZZ, split=split, return_bonds=True)
+    ref = _onsager_nn(beta)
+    for k in ("top", "bottom", "left", "right"):
+        # the 1e-8 singular-value cutoff discards weight of that order
+        assert abs(float(bonds[(0, 0)][k]) - ref) < 5e-7, k
+
+
+def _near_product(Lx, Ly, D, eps, seed):
+    rng = np.random.default_rng(seed)
+    A0 = np.zeros((Lx, Ly, 2, D, D, D, D))
+    A0[:, :, 0, 0, 0, 0, 0] = 0.8
+    A0[:, :, 1, 0, 0, 0, 0] = 0.6
+    return A0 + eps * rng.standard_normal(A0.shape)
+
+
+def test_split_agrees_with_conventional():
+    """Split and conventional CTMRG converge to the same energy (Sec. III,
+    Fig. 3a) on a generic correlated state; both are invariant under lattice
+    rotation and reflection."""
+    A0 = _near_product(1, 1, 2, 0.25, seed=5)
+    vals = []
+    for Av in (A0, I.rotate_cell_90(A0), A0.transpose(0, 1, 2, 3, 6, 5, 4)):
+        A = C.as_cell(Av)
+        vals.append(float(En.energy_per_site(A, C.split_ctmrg(A, 12, 20), HR)))
+        vals.append(float(En.energy_per_site(A, C.conv_ctmrg(A, 12, 20), HR, split=False)))
+    assert max(vals) - min(vals) < 5e-7
+
+
+def test_rotation_and_gauge_invariance():
+    """The energy of an isotropic Hamiltonian does not change when the lattice
+    is rotated by 90 degrees or when gauge matrices are put on every bond
+    (2x2 cell, J1-J2)."""
+    A = _near_product(2, 2, 2, 0.3, seed=21)
+    e0 = E_split(A, chi=12, sweeps=12, h=H, hd=0.5 * H)
+    e1 = E_split(I.rotate_cell_90(A), chi=12, sweeps=12, h=H, hd=0.5 * H)
+    e2 = E_split(I.gauge_transform_cell(A, seed=22, scale=0.2), chi=12, sweeps=12, h=H, hd=0.5 * H)
+    assert abs(e0 - e1) < 5e-7
+    assert abs(e0 - e2) < 5e-7
+
+
+def test_bond_values_physical():
+    """Every <S_i . S_j> lies in [-3/4, 1/4]."""
+    A = C.as_cell(_near_product(2, 2, 2, 0.5, seed=6))
+    env = C.split_ctmrg(A, 12, 16)
+    _, bonds = En.energy_per_site(A, env, H, H, return_bonds=True)
+    for v in bonds.values():
+        for k, val in v.items():
+            if k != "norm":
+                assert -0.75 - 1e-9 <= float(val) <= 0.25 + 1e-9
+
+
+def test_frame_maps_are_involutions():
+    A = C.as_cell(I.random_cell(2, 2, 2, 2, seed=8))
+    env = C.initial_env(A, 16)
+    for f in (C.transpose_frame, C.rot180_frame):
+        A1, e1 = f(A, env)
+        A2, e2 = f(A1, e1)
+        for x in range(2):
+            for y in range(2):
+                assert torch.equal(A2[x][y], A[x][y])
+                for k in C.SPLIT_KEYS:
+                    assert torch.equal(e2[x][y][k], env[x][y][k])
+
+
+# ---------------------------------------------------------------- gradients
+def test_svd_backward_matches_finite_differences():
+    torch.manual_seed(0)
+    M = torch.randn(6, 6, dtype=torch.float64)
+    W1 = torch.randn(6, 3, dtype=torch.float64)
+    W2 = torch.randn(6, 3, dtype=torch.float64)
+
+    def f(M):
+        U, S, V = osvd(M)
+        # sign-invariant function of the top-3 triplets
+        return ((U[:, :3] * S[:3]) @ (V[:, :3].T @ W2) * W1.sum(1, keepdim=True)).sum() + (S[:3] ** 2).sum()
+
+    Mg = M.clone().requires_grad_(True)
+    f(Mg).backward()
+    Dm = torch.randn(6, 6, dtype=torch.float64)
+    h = 1e-6
+    fd = (f(M + h * Dm) - f(M - h * Dm)) / (2 * h)
+    assert abs(float((Mg.grad * Dm).sum()) - float(fd)) < 1e-6 * max(1.0, abs(float(fd)))
+
+
+def test_oracle_gradient_matches_finite_differences():
+    """Autograd through the whole oracle (init, sweeps, energy) equals the
+    central finite difference (step 1e-5) along random directions."""
+    A0 = torch.as_tensor(I.random_cell(1, 1, 2, 2, seed=3))
+
+    def energy(At):
+        Ac = [[At[0, 0]]]
+        env = C.split_ctmrg(Ac, chi=8, sweeps=3)
+        return En.energy_per_site(Ac, env, HR)
+
+    Ag = A0.clone().requires_grad_(True)
+    energy(Ag).backward()
+    g = Ag.grad
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        v = torch.as_tensor(rng.standard_normal(A0.shape))
+        h = 1e-5
+        fd = (energy(A0 + h * v) - energy(A0 - h * v)) / (2 * h)
+        ad = (g * v).sum()
+        assert abs(float(ad) - float(fd)) < 1e-6 * max(1e-3, abs(float(fd)))
