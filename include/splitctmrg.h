@@ -1,0 +1,122 @@
+/* C ABI of the split-CTMRG engine for one GB300 GPU.
+ *
+ * Method: Naumann, Weerda, Eisert, Rizzi, Schmoll, "Variationally optimizing
+ * infinite projected entangled-pair states at large bond dimensions: a split
+ * corner transfer matrix renormalization group approach" (arXiv 2502.10298).
+ *
+ * Conventions
+ *  - All floating point data is IEEE binary64 (double), row-major.
+ *  - PEPS unit cell A_cell: [Lx][Ly][p][D][D][D][D], site (x, y) with x the row
+ *    and y the column; per site the legs are (s, up, left, down, right).  The
+ *    bra layer is the same real tensor (Sec. II.A).
+ *  - Environment of a site (Fig. 2): C1, T1ket, T1bra, C2, T2ket, T2bra, C3,
+ *    T3bra, T3ket, C4, T4bra, T4ket.  Every edge tensor is [previous, PEPS leg,
+ *    next] along the clockwise chain C1 T1k T1b C2 T2k T2b C3 T3b T3k C4 T4b
+ *    T4k; C2, C3, C4 are [previous, next] and C1 is [next (T1k), previous
+ *    (T4k)].  Environment bonds (chi_E) and interlayer bonds (chi_I) are both
+ *    chi and zero-padded to chi.
+ *  - Bond operators are real p^2 x p^2 matrices h[(t_i t_j), (s_i s_j)] with s
+ *    the ket and t the bra physical index.
+ *  - "dev" pointers are device pointers owned by the caller; "host" pointers
+ *    are host memory owned by the caller.  The library owns only the handle
+ *    (environment, workspace, stream association).
+ *  - Every call returns SCTM_OK (0) or a negative error code; a message is
+ *    available from sctm_last_error().  Calls are asynchronous on the stream
+ *    given at creation unless they return host values (those synchronise).
+ */
+#ifndef SPLITCTMRG_H
+#define SPLITCTMRG_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SCTM_API __attribute__((visibility("default")))
+#else
+#define SCTM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SCTM_OK = 0,
+  SCTM_ERR_ARG = -1,       /* invalid argument or shape                     */
+  SCTM_ERR_CUDA = -2,      /* a CUDA call failed                            */
+  SCTM_ERR_SVD_NOCONV = -3,/* a Jacobi SVD did not converge                 */
+  SCTM_ERR_NONFINITE = -4, /* NaN or Inf in a result                        */
+  SCTM_ERR_OOM = -5,       /* device workspace too small                    */
+  SCTM_ERR_STATE = -6      /* call order (e.g. move before init)            */
+};
+
+typedef struct sctm_ctx* sctm_handle;
+
+typedef struct {
+  int Lx, Ly;            /* unit cell                                        */
+  int p;                 /* physical dimension                               */
+  int D;                 /* bulk bond dimension chi_B                        */
+  int chi;               /* environment and interlayer bond dimension        */
+  int precision;         /* 0 = FP64 throughout                              */
+  double svd_cutoff;     /* relative singular-value cutoff of projectors (<=0: 1e-8) */
+  double lorentz_eps;    /* Lorentzian broadening of the SVD adjoint (<=0: 1e-36 s_max^4) */
+  size_t workspace_bytes;/* device workspace; 0 = library default          */
+} sctm_config;
+
+/* Create a handle.  stream: a cudaStream_t (NULL = legacy default stream). */
+SCTM_API int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out);
+SCTM_API int sctm_destroy(sctm_handle h);
+SCTM_API const char* sctm_last_error(sctm_handle h);
+
+/* Load A_cell (dev) and build the initial environment from the double-layer
+ * contractions of the neighbouring tensors (corners and edges of the norm
+ * network with their outward legs traced), each edge split into its ket and
+ * bra halves by a truncated SVD (Sec. II.B: a ket/bra pair contracted over
+ * the interlayer bond is the conventional edge).  Requires D*D <= chi. */
+SCTM_API int split_ctmrg_init(sctm_handle h, const double* A_cell_dev);
+
+/* One directional move over every column/row of the cell (Sec. II.B,
+ * Eqs. splitCTMRG_C1, _C4, _Tket, _Tbra): dir 0 left, 1 top, 2 right,
+ * 3 bottom.  Each new environment tensor is divided by its max |entry|. */
+SCTM_API int split_ctmrg_move(sctm_handle h, int dir);
+
+/* n full directional steps (left, top, right, bottom) = n sweeps. */
+SCTM_API int split_ctmrg_sweeps(sctm_handle h, int n);
+
+/* Projector pair of one cut of the move `dir` at the current environment,
+ * without moving.  colour: 0 green, 1 teal, 2 yellow, 3 red (Sec. II.B, App. A).
+ * (x, y) is the site in the frame of the move (the left-move frame is the
+ * lattice itself).  P_up_dev: [chi][alpha], P_dn_dev: [alpha][chi] with
+ * alpha = chi*D (green, teal, yellow) or chi*p*D (red); s_host receives the
+ * chi largest singular values of the decomposed core. */
+SCTM_API int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P_up_dev, double* P_dn_dev,
+                     double* s_host);
+
+/* Energy per site from 2x2 patches: (1/N) sum over patch anchors of half of the
+ * four nearest-neighbour bond values plus both diagonal bond values.
+ * h_nn_host: p^2 x p^2 nearest-neighbour operator; h_diag_host: diagonal
+ * operator or NULL.  Synchronises and writes *e_per_site (host). */
+SCTM_API int energy_2x2(sctm_handle h, const double* h_nn_host, const double* h_diag_host, double* e_per_site);
+
+/* Energy and its gradient with respect to A_cell: initial environment,
+ * `sweeps` full steps, 2x2 energy, then the reverse pass through all of it
+ * (per-sweep checkpoints, hand-written adjoints, SVD adjoint with Lorentzian
+ * broadening).  grad_dev has the layout of A_cell.  Leaves the converged
+ * environment in the handle. */
+SCTM_API int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const double* h_nn_host,
+                const double* h_diag_host, double* e_per_site, double* grad_dev);
+
+/* Same with host buffers: copies A_cell_host in and the gradient out. */
+SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const double* h_nn_host,
+                     const double* h_diag_host, double* e_per_site, double* grad_host);
+
+/* Environment of site (x, y) into out_dev, packed in the order C1 T1k T1b C2
+ * T2k T2b C3 T3b T3k C4 T4b T4k (chi^2 or chi*D*chi doubles each). */
+SCTM_API int sctm_get_env(sctm_handle h, int x, int y, double* out_dev);
+
+/* Device workspace high-water mark in bytes. */
+SCTM_API int sctm_workspace_high_water(sctm_handle h, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLITCTMRG_H */

@@ -1,0 +1,216 @@
+"""ctypes binding of libsplitctmrg.so (names follow include/splitctmrg.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+__all__ = [
+    "load_library", "Config", "sctm_create", "sctm_destroy", "split_ctmrg_init", "split_ctmrg_move",
+    "split_ctmrg_sweeps", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
+    "sctm_get_env", "sctm_workspace_high_water", "SplitCTMRG", "ENV_KEYS", "SctmError",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsplitctmrg.so")
+ENV_KEYS = ("C1", "T1k", "T1b", "C2", "T2k", "T2b", "C3", "T3b", "T3k", "C4", "T4b", "T4k")
+_ERRORS = {-1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_SVD_NOCONV", -4: "ERR_NONFINITE", -5: "ERR_OOM",
+           -6: "ERR_STATE"}
+
+
+class SctmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("p", ctypes.c_int), ("D", ctypes.c_int),
+                ("chi", ctypes.c_int), ("precision", ctypes.c_int), ("svd_cutoff", ctypes.c_double),
+                ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the in-tree library (build it with ``paper_2502_10298_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsplitctmrg.so not found at {path}; run paper_2502_10298_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "sctm_create": (i, [ctypes.POINTER(Config), vp, ctypes.POINTER(vp)]),
+        "sctm_destroy": (i, [vp]),
+        "sctm_last_error": (ctypes.c_char_p, [vp]),
+        "split_ctmrg_init": (i, [vp, vp]),
+        "split_ctmrg_move": (i, [vp, i]),
+        "split_ctmrg_sweeps": (i, [vp, i]),
+        "ctmrg_projectors": (i, [vp, i, i, i, i, vp, vp, _dp]),
+        "energy_2x2": (i, [vp, _dp, _dp, _dp]),
+        "energy_grad": (i, [vp, vp, i, _dp, _dp, _dp, vp]),
+        "energy_grad_host": (i, [vp, _dp, i, _dp, _dp, _dp, _dp]),
+        "sctm_get_env": (i, [vp, i, i, vp]),
+        "sctm_workspace_high_water": (i, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(h, rc):
+    if rc != 0:
+        msg = _lib.sctm_last_error(h).decode() if h else "create failed"
+        raise SctmError(rc, msg)
+
+
+def _hp(a):
+    """host float64 array -> (keep-alive array, pointer)"""
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return arr, arr.ctypes.data_as(_dp)
+
+
+def sctm_create(Lx, Ly, p, D, chi, precision=0, svd_cutoff=0.0, lorentz_eps=0.0, workspace_bytes=0,
+                stream=None):
+    lib = load_library()
+    cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    h = ctypes.c_void_p()
+    rc = lib.sctm_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(h))
+    if rc != 0:
+        raise SctmError(rc, "sctm_create failed")
+    return h
+
+
+def sctm_destroy(h):
+    _check(h, _lib.sctm_destroy(h))
+
+
+def _dev(t: torch.Tensor):
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "need a contiguous CUDA float64 tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def split_ctmrg_init(h, A_cell: torch.Tensor):
+    _check(h, _lib.split_ctmrg_init(h, _dev(A_cell)))
+
+
+def split_ctmrg_move(h, direction: int):
+    _check(h, _lib.split_ctmrg_move(h, int(direction)))
+
+
+def split_ctmrg_sweeps(h, n: int):
+    _check(h, _lib.split_ctmrg_sweeps(h, int(n)))
+
+
+def ctmrg_projectors(h, direction, x, y, colour, chi, alpha):
+    up = torch.empty((chi, alpha), dtype=torch.float64, device="cuda")
+    dn = torch.empty((alpha, chi), dtype=torch.float64, device="cuda")
+    s = np.zeros(chi)
+    _check(h, _lib.ctmrg_projectors(h, direction, x, y, colour, _dev(up), _dev(dn), s.ctypes.data_as(_dp)))
+    return up, dn, s
+
+
+def energy_2x2(h, h_nn, h_diag=None) -> float:
+    a, pa = _hp(h_nn)
+    b, pb = _hp(h_diag)
+    e = ctypes.c_double()
+    _check(h, _lib.energy_2x2(h, pa, pb, ctypes.byref(e)))
+    return e.value
+
+
+def energy_grad(h, A_cell: torch.Tensor, sweeps: int, h_nn, h_diag=None):
+    a, pa = _hp(h_nn)
+    b, pb = _hp(h_diag)
+    g = torch.empty_like(A_cell)
+    e = ctypes.c_double()
+    _check(h, _lib.energy_grad(h, _dev(A_cell), int(sweeps), pa, pb, ctypes.byref(e), _dev(g)))
+    return e.value, g
+
+
+def energy_grad_host(h, A_cell: np.ndarray, sweeps: int, h_nn, h_diag=None, grad_out: np.ndarray = None):
+    A_cell = np.ascontiguousarray(A_cell, dtype=np.float64)
+    if grad_out is None:
+        grad_out = np.empty_like(A_cell)
+    a, pa = _hp(h_nn)
+    b, pb = _hp(h_diag)
+    e = ctypes.c_double()
+    _check(h, _lib.energy_grad_host(h, A_cell.ctypes.data_as(_dp), int(sweeps), pa, pb, ctypes.byref(e),
+                                    grad_out.ctypes.data_as(_dp)))
+    return e.value, grad_out
+
+
+def sctm_get_env(h, x, y, chi, D):
+    sizes = [chi * chi if k[0] == "C" else chi * D * chi for k in ENV_KEYS]
+    buf = torch.empty(sum(sizes), dtype=torch.float64, device="cuda")
+    _check(h, _lib.sctm_get_env(h, x, y, _dev(buf)))
+    out, off = {}, 0
+    for k, n in zip(ENV_KEYS, sizes):
+        shape = (chi, chi) if k[0] == "C" else (chi, D, chi)
+        out[k] = buf[off:off + n].view(shape)
+        off += n
+    return out
+
+
+def sctm_workspace_high_water(h) -> int:
+    v = ctypes.c_size_t()
+    _check(h, _lib.sctm_workspace_high_water(h, ctypes.byref(v)))
+    return v.value
+
+
+class SplitCTMRG:
+    """Owning wrapper: ``with SplitCTMRG(Lx, Ly, p, D, chi) as s: ...``"""
+
+    def __init__(self, Lx, Ly, p, D, chi, **kw):
+        self.Lx, self.Ly, self.p, self.D, self.chi = Lx, Ly, p, D, chi
+        self.h = sctm_create(Lx, Ly, p, D, chi, **kw)
+
+    def close(self):
+        if self.h is not None:
+            sctm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, A):
+        split_ctmrg_init(self.h, A)
+
+    def move(self, d):
+        split_ctmrg_move(self.h, d)
+
+    def sweeps(self, n):
+        split_ctmrg_sweeps(self.h, n)
+
+    def env(self, x, y):
+        return sctm_get_env(self.h, x, y, self.chi, self.D)
+
+    def energy(self, h_nn, h_diag=None):
+        return energy_2x2(self.h, h_nn, h_diag)
+
+    def energy_grad(self, A, sweeps, h_nn, h_diag=None):
+        return energy_grad(self.h, A, sweeps, h_nn, h_diag)
+
+    def projectors(self, direction, x, y, colour):
+        alpha = self.chi * self.D * (self.p if colour == 3 else 1)
+        return ctmrg_projectors(self.h, direction, x, y, colour, self.chi, alpha)

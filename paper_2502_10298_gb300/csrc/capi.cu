@@ -1,0 +1,473 @@
+// C ABI of the engine (declared in include/splitctmrg.h).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "../../include/splitctmrg.h"
+#include "ctmrg.h"
+
+using namespace sctm;
+
+struct sctm_ctx {
+  Params P;
+  Ctx c;
+  std::string err;
+  bool ready = false;
+  // persistent device memory: A (+grad), environment store, checkpoints
+  double* A = nullptr;
+  double* Agrad = nullptr;
+  double* store = nullptr;       // environment of every site
+  long long env_site = 0;        // doubles per site
+  long long key_off[NKEY] = {0};
+  int key_shape[NKEY][3] = {{0}};
+  int key_nd[NKEY] = {0};
+  Cell cell;
+  ~sctm_ctx() {
+    if (A) cudaFree(A);
+    if (Agrad) cudaFree(Agrad);
+    if (store) cudaFree(store);
+    if (c.partial) cudaFree(c.partial);
+    if (c.svd_status) cudaFree(c.svd_status);
+  }
+};
+
+namespace {
+
+int fail(sctm_handle h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+template <typename F>
+int guard(sctm_handle h, F&& f) {
+  if (!h) return SCTM_ERR_ARG;
+  try {
+    f();
+    return SCTM_OK;
+  } catch (const ArgError& e) {
+    std::string m = e.what();
+    return fail(h, m.find("workspace exhausted") != std::string::npos ? SCTM_ERR_OOM : SCTM_ERR_ARG, m);
+  } catch (const CudaError& e) {
+    return fail(h, SCTM_ERR_CUDA, e.what());
+  } catch (const std::exception& e) {
+    std::string m = e.what();
+    if (m.find("no convergence") != std::string::npos) return fail(h, SCTM_ERR_SVD_NOCONV, m);
+    if (m.find("non-finite") != std::string::npos) return fail(h, SCTM_ERR_NONFINITE, m);
+    return fail(h, SCTM_ERR_ARG, m);
+  }
+}
+
+long long site_index(sctm_handle h, int x, int y) {
+  int Lx = h->P.Lx, Ly = h->P.Ly;
+  return (long long)((x % Lx + Lx) % Lx) * Ly + ((y % Ly + Ly) % Ly);
+}
+
+Tensor key_view(sctm_handle h, double* base, int x, int y, int k) {
+  Tensor t;
+  t.data = base + site_index(h, x, y) * h->env_site + h->key_off[k];
+  t.nd = h->key_nd[k];
+  long long st = 1;
+  for (int i = t.nd - 1; i >= 0; --i) t.shape[i] = h->key_shape[k][i], t.stride[i] = st, st *= t.shape[i];
+  return t;
+}
+
+// A views of the persistent buffer (gradient pointer aligned with the data)
+void bind_A(sctm_handle h, bool with_grad) {
+  const int p = h->P.p, D = h->P.D;
+  const long long per = (long long)p * D * D * D * D;
+  h->cell.Lx = h->P.Lx;
+  h->cell.Ly = h->P.Ly;
+  h->cell.A.resize(h->P.Lx * h->P.Ly);
+  h->cell.env.resize(h->P.Lx * h->P.Ly);
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y) {
+      Tensor t;
+      long long off = (x * (long long)h->P.Ly + y) * per;
+      t.data = h->A + off;
+      t.grad = with_grad ? h->Agrad + off : nullptr;
+      t.nd = 5;
+      int s[5] = {p, D, D, D, D};
+      long long st = 1;
+      for (int i = 4; i >= 0; --i) t.shape[i] = s[i], t.stride[i] = st, st *= s[i];
+      h->cell.a(x, y) = t;
+    }
+}
+
+// copy the current environment handles into `dst` (packed store layout)
+void save_env(sctm_handle h, double* dst) {
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y)
+      for (int k = 0; k < NKEY; ++k) {
+        Tensor d = key_view(h, dst, x, y, k);
+        Tensor& s = h->cell.e(x, y)[k];
+        if (s.data == d.data) continue;
+        bool t = h->c.tape.active;
+        h->c.tape.active = false;
+        copy_into(h->c, s, d);
+        h->c.tape.active = t;
+      }
+}
+
+// point the environment handles at the store (no gradient buffers)
+void bind_store(sctm_handle h, double* base) {
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y)
+      for (int k = 0; k < NKEY; ++k) h->cell.e(x, y)[k] = key_view(h, base, x, y, k);
+}
+
+// leaves for a taped region: arena copies of `base` with zeroed gradients
+void bind_leaves(sctm_handle h, double* base) {
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y)
+      for (int k = 0; k < NKEY; ++k) {
+        Tensor src = key_view(h, base, x, y, k);
+        Tensor t = h->c.empty_shape(src.shape, src.nd);   // tape active -> zeroed grad
+        bool a = h->c.tape.active;
+        h->c.tape.active = false;
+        copy_into(h->c, src, t);
+        h->c.tape.active = a;
+        h->cell.e(x, y)[k] = t;
+      }
+}
+
+// gradient buffers of the current handles <- / -> packed layout
+void seed_env_grad(sctm_handle h, const double* g) {
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y)
+      for (int k = 0; k < NKEY; ++k) {
+        Tensor s = key_view(h, const_cast<double*>(g), x, y, k);
+        Tensor& t = h->cell.e(x, y)[k];
+        SCTM_CHECK(t.grad, "environment handle without gradient buffer");
+        Tensor gv = t;
+        gv.data = t.grad;
+        gv.grad = nullptr;
+        bool a = h->c.tape.active;
+        h->c.tape.active = false;
+        copy_into(h->c, s, gv);
+        h->c.tape.active = a;
+      }
+}
+
+void read_env_grad(sctm_handle h, double* g) {
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y)
+      for (int k = 0; k < NKEY; ++k) {
+        Tensor d = key_view(h, g, x, y, k);
+        Tensor& t = h->cell.e(x, y)[k];
+        Tensor gv = t;
+        gv.data = t.grad;
+        gv.grad = nullptr;
+        bool a = h->c.tape.active;
+        h->c.tape.active = false;
+        copy_into(h->c, gv, d);
+        h->c.tape.active = a;
+      }
+}
+
+void check_svd(sctm_handle h) {
+  // the SVD kernels record -1 in the status word when they ran out of sweeps
+  int st = 0;
+  SCTM_CUDA(cudaMemcpyAsync(&st, h->c.svd_status, sizeof(int), cudaMemcpyDeviceToHost, h->c.stream));
+  SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  if (st < 0) {
+    SCTM_CUDA(cudaMemsetAsync(h->c.svd_status, 0, sizeof(int), h->c.stream));
+    throw std::runtime_error("svd: no convergence");
+  }
+}
+
+void sweep_untaped(sctm_handle h) {
+  for (int d = 0; d < 4; ++d) {
+    size_t mk = h->c.arena.mark();
+    move(h->c, h->P, h->cell, d);
+    save_env(h, h->store);
+    bind_store(h, h->store);
+    h->c.arena.release(mk);
+  }
+}
+
+double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed) {
+  std::vector<EnergyTerm> terms = energy_terms(h->c, h->P, h->cell, hn, hd);
+  std::vector<double> nums(terms.size()), dens(terms.size());
+  for (size_t i = 0; i < terms.size(); ++i) {
+    SCTM_CUDA(cudaMemcpyAsync(&nums[i], terms[i].num.data, sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+    SCTM_CUDA(cudaMemcpyAsync(&dens[i], terms[i].den.data, sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+  }
+  SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  double E = 0;
+  for (size_t i = 0; i < terms.size(); ++i) E += terms[i].w * nums[i] / dens[i];
+  if (!std::isfinite(E)) throw std::runtime_error("non-finite energy");
+  if (seed) {
+    // dE/dnum = w/den ; dE/dden = -w num/den^2 (accumulated per shared den)
+    std::vector<std::pair<double*, double>> gs;
+    std::vector<double> hostv;
+    for (size_t i = 0; i < terms.size(); ++i) {
+      double gn = terms[i].w / dens[i];
+      double gd = -terms[i].w * nums[i] / (dens[i] * dens[i]);
+      SCTM_CHECK(terms[i].num.grad && terms[i].den.grad, "energy terms without gradient buffers");
+      gs.push_back({terms[i].num.grad, gn});
+      gs.push_back({terms[i].den.grad, gd});
+    }
+    // accumulate on host per distinct pointer, then upload
+    std::vector<std::pair<double*, double>> acc;
+    for (auto& g : gs) {
+      bool found = false;
+      for (auto& a : acc)
+        if (a.first == g.first) a.second += g.second, found = true;
+      if (!found) acc.push_back(g);
+    }
+    hostv.resize(acc.size());
+    for (size_t i = 0; i < acc.size(); ++i) hostv[i] = acc[i].second;
+    for (size_t i = 0; i < acc.size(); ++i)
+      SCTM_CUDA(cudaMemcpyAsync(acc[i].first, &hostv[i], sizeof(double), cudaMemcpyHostToDevice, h->c.stream));
+    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  }
+  return E;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
+  if (!cfg || !out) return SCTM_ERR_ARG;
+  auto h = std::make_unique<sctm_ctx>();
+  int rc = guard(h.get(), [&]() {
+    SCTM_CHECK(cfg->Lx >= 1 && cfg->Ly >= 1 && cfg->p >= 1 && cfg->D >= 1 && cfg->chi >= 1, "bad dimensions");
+    SCTM_CHECK(cfg->D * cfg->D <= cfg->chi, "chi must be >= D^2");
+    SCTM_CHECK(cfg->precision == 0, "only precision 0 (FP64) is available");
+    Params& P = h->P;
+    P.Lx = cfg->Lx, P.Ly = cfg->Ly, P.p = cfg->p, P.D = cfg->D, P.chi = cfg->chi;
+    if (cfg->svd_cutoff > 0) P.cutoff = cfg->svd_cutoff;
+    if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
+    h->c.stream = (cudaStream_t)stream;
+    const int chi = P.chi, D = P.D;
+    long long off = 0;
+    for (int k = 0; k < NKEY; ++k) {
+      bool corner = (k == C1 || k == C2 || k == C3 || k == C4);
+      h->key_off[k] = off;
+      if (corner) {
+        h->key_nd[k] = 2, h->key_shape[k][0] = chi, h->key_shape[k][1] = chi;
+        off += (long long)chi * chi;
+      } else {
+        h->key_nd[k] = 3, h->key_shape[k][0] = chi, h->key_shape[k][1] = D, h->key_shape[k][2] = chi;
+        off += (long long)chi * D * chi;
+      }
+    }
+    h->env_site = off;
+    const long long N = (long long)P.Lx * P.Ly;
+    const long long nA = N * P.p * (long long)D * D * D * D;
+    SCTM_CUDA(cudaMalloc(&h->A, nA * sizeof(double)));
+    SCTM_CUDA(cudaMalloc(&h->Agrad, nA * sizeof(double)));
+    SCTM_CUDA(cudaMalloc(&h->store, N * off * sizeof(double)));
+    SCTM_CUDA(cudaMemset(h->store, 0, N * off * sizeof(double)));
+    SCTM_CUDA(cudaMalloc(&h->c.partial, 4096 * sizeof(double)));
+    SCTM_CUDA(cudaMalloc(&h->c.svd_status, 64 * sizeof(int)));
+    SCTM_CUDA(cudaMemset(h->c.svd_status, 0, 64 * sizeof(int)));
+    size_t ws = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)4 << 30);
+    h->c.arena.reserve(ws);
+    bind_A(h.get(), false);
+    bind_store(h.get(), h->store);
+  });
+  if (rc != SCTM_OK) {
+    // report through a static buffer: the handle is released
+    static thread_local std::string last;
+    last = h->err;
+    return rc;
+  }
+  *out = h.release();
+  return SCTM_OK;
+}
+
+int sctm_destroy(sctm_handle h) {
+  if (!h) return SCTM_ERR_ARG;
+  cudaStreamSynchronize(h->c.stream);
+  delete h;
+  return SCTM_OK;
+}
+
+const char* sctm_last_error(sctm_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+int split_ctmrg_init(sctm_handle h, const double* A_cell_dev) {
+  return guard(h, [&]() {
+    SCTM_CHECK(A_cell_dev, "A_cell is null");
+    const long long nA = (long long)h->P.Lx * h->P.Ly * h->P.p * (long long)h->P.D * h->P.D * h->P.D * h->P.D;
+    SCTM_CUDA(cudaMemcpyAsync(h->A, A_cell_dev, nA * sizeof(double), cudaMemcpyDeviceToDevice, h->c.stream));
+    bind_A(h, false);
+    h->c.tape.active = false;
+    size_t mk = h->c.arena.mark();
+    init_env(h->c, h->P, h->cell);
+    save_env(h, h->store);
+    bind_store(h, h->store);
+    h->c.arena.release(mk);
+    h->ready = true;
+  });
+}
+
+int split_ctmrg_move(sctm_handle h, int dir) {
+  return guard(h, [&]() {
+    SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
+    SCTM_CHECK(dir >= 0 && dir < 4, "dir must be 0..3");
+    size_t mk = h->c.arena.mark();
+    move(h->c, h->P, h->cell, dir);
+    save_env(h, h->store);
+    bind_store(h, h->store);
+    h->c.arena.release(mk);
+  });
+}
+
+int split_ctmrg_sweeps(sctm_handle h, int n) {
+  return guard(h, [&]() {
+    SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
+    for (int i = 0; i < n; ++i) sweep_untaped(h);
+    check_svd(h);
+  });
+}
+
+int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P_up_dev, double* P_dn_dev,
+                     double* s_host) {
+  return guard(h, [&]() {
+    SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
+    SCTM_CHECK(dir >= 0 && dir < 4 && colour >= 0 && colour < 4, "bad dir or colour");
+    size_t mk = h->c.arena.mark();
+    Cell fr;
+    if (dir == 0) fr = h->cell;
+    else if (dir == 1) fr = frame_transpose(h->cell);
+    else if (dir == 2) fr = frame_rot180(h->cell);
+    else {
+      Cell t = frame_rot180(h->cell);
+      fr = frame_transpose(t);
+    }
+    ColumnProj cp;
+    column_projectors(h->c, h->P, fr, ((y % fr.Ly) + fr.Ly) % fr.Ly, cp);
+    int xi = ((x % fr.Lx) + fr.Lx) % fr.Lx;
+    const ProjPair& pp = colour == 0 ? cp.g[xi] : colour == 1 ? cp.t[xi] : colour == 2 ? cp.y[xi] : cp.r[xi];
+    long long n = pp.up.numel();
+    SCTM_CUDA(cudaMemcpyAsync(P_up_dev, pp.up.data, n * sizeof(double), cudaMemcpyDeviceToDevice, h->c.stream));
+    SCTM_CUDA(cudaMemcpyAsync(P_dn_dev, pp.dn.data, n * sizeof(double), cudaMemcpyDeviceToDevice, h->c.stream));
+    if (s_host)
+      SCTM_CUDA(cudaMemcpyAsync(s_host, pp.s.data, h->P.chi * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+    h->c.arena.release(mk);
+  });
+}
+
+int energy_2x2(sctm_handle h, const double* h_nn_host, const double* h_diag_host, double* e_per_site) {
+  return guard(h, [&]() {
+    SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
+    SCTM_CHECK(h_nn_host && e_per_site, "null argument");
+    size_t mk = h->c.arena.mark();
+    h->c.tape.active = false;
+    *e_per_site = energy_value(h, h_nn_host, h_diag_host, false);
+    h->c.arena.release(mk);
+  });
+}
+
+int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const double* h_nn_host,
+                const double* h_diag_host, double* e_per_site, double* grad_dev) {
+  return guard(h, [&]() {
+    SCTM_CHECK(A_cell_dev && h_nn_host && e_per_site && grad_dev, "null argument");
+    SCTM_CHECK(sweeps >= 0, "sweeps must be >= 0");
+    Ctx& c = h->c;
+    const Params& P = h->P;
+    const long long N = (long long)P.Lx * P.Ly;
+    const long long nA = N * P.p * (long long)P.D * P.D * P.D * P.D;
+    const long long nE = N * h->env_site;
+    SCTM_CUDA(cudaMemcpyAsync(h->A, A_cell_dev, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    SCTM_CUDA(cudaMemsetAsync(h->Agrad, 0, nA * sizeof(double), c.stream));
+    size_t base = c.arena.mark();
+    // checkpoints of the environment at the start of every sweep (+ final)
+    double* ck = c.arena.alloc(nE * (sweeps + 1));
+    double* gbuf = c.arena.alloc(nE);
+    size_t top = c.arena.mark();
+    // forward: init + sweeps, untaped
+    c.tape.active = false;
+    bind_A(h, false);
+    init_env(c, P, h->cell);
+    save_env(h, ck);
+    bind_store(h, ck);
+    c.arena.release(top);
+    for (int s = 0; s < sweeps; ++s) {
+      for (int d = 0; d < 4; ++d) {
+        move(c, P, h->cell, d);
+        save_env(h, ck + (s + 1) * nE);   // in-sweep moves write into the next checkpoint
+        bind_store(h, ck + (s + 1) * nE);
+        c.arena.release(top);
+      }
+    }
+    check_svd(h);
+    // energy on the final environment, taped
+    bind_A(h, true);
+    c.tape.active = true;
+    bind_leaves(h, ck + sweeps * nE);
+    *e_per_site = energy_value(h, h_nn_host, h_diag_host, true);
+    c.tape.backward();
+    read_env_grad(h, gbuf);
+    c.tape.active = false;
+    c.arena.release(top);
+    // reverse through the sweeps, one checkpointed sweep at a time
+    for (int s = sweeps - 1; s >= 0; --s) {
+      c.tape.active = true;
+      bind_leaves(h, ck + s * nE);
+      std::vector<SiteEnv> leaves = h->cell.env;
+      for (int d = 0; d < 4; ++d) move(c, P, h->cell, d);
+      seed_env_grad(h, gbuf);
+      c.tape.backward();
+      h->cell.env = leaves;
+      read_env_grad(h, gbuf);
+      c.tape.active = false;
+      c.arena.release(top);
+    }
+    // reverse through the initial environment
+    c.tape.active = true;
+    init_env(c, P, h->cell);
+    seed_env_grad(h, gbuf);
+    c.tape.backward();
+    c.tape.active = false;
+    check_svd(h);
+    SCTM_CUDA(cudaMemcpyAsync(grad_dev, h->Agrad, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    // leave the converged environment in the store
+    bind_A(h, false);
+    bind_store(h, ck + sweeps * nE);
+    save_env(h, h->store);
+    bind_store(h, h->store);
+    SCTM_CUDA(cudaStreamSynchronize(c.stream));
+    c.arena.release(base);
+    h->ready = true;
+  });
+}
+
+int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const double* h_nn_host,
+                     const double* h_diag_host, double* e_per_site, double* grad_host) {
+  return guard(h, [&]() {
+    SCTM_CHECK(A_cell_host && grad_host, "null argument");
+    const Params& P = h->P;
+    const long long nA = (long long)P.Lx * P.Ly * P.p * (long long)P.D * P.D * P.D * P.D;
+    size_t mk = h->c.arena.mark();
+    double* a = h->c.arena.alloc(nA);
+    double* g = h->c.arena.alloc(nA);
+    size_t inner = h->c.arena.mark();
+    SCTM_CUDA(cudaMemcpyAsync(a, A_cell_host, nA * sizeof(double), cudaMemcpyHostToDevice, h->c.stream));
+    int rc = energy_grad(h, a, sweeps, h_nn_host, h_diag_host, e_per_site, g);
+    if (rc != SCTM_OK) throw std::runtime_error(h->err);
+    (void)inner;
+    SCTM_CUDA(cudaMemcpyAsync(grad_host, g, nA * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+    h->c.arena.release(mk);
+  });
+}
+
+int sctm_get_env(sctm_handle h, int x, int y, double* out_dev) {
+  return guard(h, [&]() {
+    SCTM_CHECK(out_dev, "null argument");
+    SCTM_CUDA(cudaMemcpyAsync(out_dev, h->store + site_index(h, x, y) * h->env_site, h->env_site * sizeof(double),
+                              cudaMemcpyDeviceToDevice, h->c.stream));
+    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  });
+}
+
+int sctm_workspace_high_water(sctm_handle h, size_t* bytes) {
+  return guard(h, [&]() { *bytes = h->c.arena.high_water(); });
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Strided batched tensor contraction on CUDA cores (FP64 / FP32 storage).
+//
+// Every pairwise contraction of the split-CTMRG networks (absorption
+// equations, rho networks, M = rho^B rho^T, projector application) is
+// C[b,m,n] = alpha * sum_k A[b,m,k] B[b,k,n] + beta * C[b,m,n], where each of
+// b, m, n, k is a group of tensor legs with arbitrary strides.  Index
+// permutations are therefore never materialised: a tile loader gathers
+// operand elements through per-tile offset tables kept in shared memory.
+#include "common.h"
+#include "kernels.h"
+
+namespace sctm {
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int TX = BN / TN;
+  __shared__ long long offAm[BM], offCm[BM], offBn[BN], offCn[BN];
+  __shared__ long long offAk[BK], offBk[BK];
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+
+  const int tid = threadIdx.x;
+  const long long b = blockIdx.z;
+  const long long m0 = (long long)blockIdx.y * BM;
+  const long long n0 = (long long)blockIdx.x * BN;
+  const long long boA = group_offset(d.bat, d.bat.sa, b);
+  const long long boB = group_offset(d.bat, d.bat.sb, b);
+  const long long boC = group_offset(d.bat, d.bat.sc, b);
+  for (int i = tid; i < BM; i += NT) {
+    long long m = m0 + i;
+    if (m < d.M) {
+      offAm[i] = boA + group_offset(d.m, d.m.sa, m);
+      offCm[i] = boC + group_offset(d.m, d.m.sc, m);
+    } else {
+      offAm[i] = -1;
+      offCm[i] = -1;
+    }
+  }
+  for (int i = tid; i < BN; i += NT) {
+    long long n = n0 + i;
+    if (n < d.N) {
+      offBn[i] = boB + group_offset(d.n, d.n.sb, n);
+      offCn[i] = group_offset(d.n, d.n.sc, n);
+    } else {
+      offBn[i] = -1;
+      offCn[i] = -1;
+    }
+  }
+  const int ty = tid / TX, tx = tid % TX;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  for (long long k0 = 0; k0 < d.K; k0 += BK) {
+    __syncthreads();
+    if (tid < BK) {
+      long long k = k0 + tid;
+      offAk[tid] = (k < d.K) ? group_offset(d.k, d.k.sa, k) : -1;
+      offBk[tid] = (k < d.K) ? group_offset(d.k, d.k.sb, k) : -1;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      int mm, kk;
+      if (d.a_k_inner) { kk = idx % BK; mm = idx / BK; }
+      else { mm = idx % BM; kk = idx / BM; }
+      long long om = offAm[mm], ok = offAk[kk];
+      As[kk][mm] = (om >= 0 && ok >= 0) ? A[om + ok] : T(0);
+    }
+    for (int idx = tid; idx < BN * BK; idx += NT) {
+      int nn, kk;
+      if (d.b_n_inner) { nn = idx % BN; kk = idx / BN; }
+      else { kk = idx % BK; nn = idx / BK; }
+      long long on = offBn[nn], ok = offBk[kk];
+      Bs[kk][nn] = (on >= 0 && ok >= 0) ? B[on + ok] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + j * TX];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+  }
+  __syncthreads();
+  const T alpha = (T)d.alpha, beta = (T)d.beta;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int mm = ty + i * (BM / TM);
+    long long om = offCm[mm];
+    if (om < 0) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int nn = tx + j * TX;
+      long long on = offCn[nn];
+      if (on < 0) continue;
+      T v = alpha * acc[i][j];
+      if (d.beta != 0.0) v += beta * C[om + on];
+      C[om + on] = v;
+    }
+  }
+}
+
+template <typename T>
+void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s) {
+  if (d.M == 0 || d.N == 0 || d.B == 0) return;
+  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+  dim3 grid((unsigned)((d.N + BN - 1) / BN), (unsigned)((d.M + BM - 1) / BM), (unsigned)d.B);
+  SCTM_CHECK(grid.y <= 65535 && grid.z <= 65535, "contraction too large for grid");
+  contract_kernel<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+template void launch_contract<double>(const ContractDesc&, const double*, const double*, double*, cudaStream_t);
+template void launch_contract<float>(const ContractDesc&, const float*, const float*, float*, cudaStream_t);
+
+}  // namespace sctm

@@ -1,0 +1,616 @@
+// Split-CTMRG engine (see ctmrg.h).
+//
+// Paper: Naumann et al., arXiv 2502.10298.  Environment: Fig. 2.  Left move:
+// Eqs. (splitCTMRG_C1), (splitCTMRG_C4), (splitCTMRG_Tket), (splitCTMRG_Tbra).
+// Projectors: Sec. II.B (Fig. 3) and App. A (Figs. 7-9).  The other three
+// moves are left moves in a transposed or 180-degree rotated frame; frames are
+// pure stride/handle permutations, so they cost nothing on the device.
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "ctmrg.h"
+
+namespace sctm {
+
+// ------------------------------------------------------------------ projector
+// rhoT: alpha x beta (upper half), rhoB: beta x alpha (lower half).
+// M = rhoB rhoT has rank <= alpha; when alpha < beta both halves are reduced
+// first (App. A), here through their Gram matrices:
+//   rhoT rhoT^T = L_T L_T^T, rhoB^T rhoB = L_B L_B^T (eigendecompositions),
+//   K = L_B^T L_T = U S V^T,  P_up = S^-1/2 U^T L_B^T,  P_dn = L_T V S^-1/2,
+// which equals S^-1/2 U~^T rhoB and rhoT V~ S^-1/2 for the full M.
+ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB) {
+  const int a = rhoT.shape[0], b = rhoT.shape[1];
+  SCTM_CHECK(rhoB.shape[0] == b && rhoB.shape[1] == a, "projector: rho shapes do not match");
+  Tensor left, right;  // core = left @ right  (n x n), P_up = w U^T left, P_dn = right V w
+  if (a < b) {
+    Tensor GT = einsum(c, "ab,cb->ac", rhoT, rhoT);
+    Tensor GB = einsum(c, "ba,bc->ac", rhoB, rhoB);
+    SVDResult eT = svd(c, GT, P.eps_l);
+    SVDResult eB = svd(c, GB, P.eps_l);
+    Tensor qT = spectrum_map(c, eT.S, a, P.gram_cutoff, 1);
+    Tensor qB = spectrum_map(c, eB.S, a, P.gram_cutoff, 1);
+    Tensor LT = scale_dim(c, eT.V, 1, qT);   // a x a
+    Tensor LB = scale_dim(c, eB.V, 1, qB);
+    left = LB.rev();                         // L_B^T
+    right = LT;
+  } else {
+    left = rhoB;
+    right = rhoT;
+  }
+  Tensor M = einsum(c, "ik,kj->ij", left, right);
+  const int n = M.shape[0];
+  const int k = P.chi;
+  SCTM_CHECK(k <= n, "projector: chi larger than the decomposed space");
+  SVDResult r = svd(c, M, P.eps_l);
+  Tensor w = spectrum_map(c, r.S, k, P.cutoff, 0);
+  Tensor Uk = r.U, Vk = r.V;
+  Uk.shape[1] = k;   // first k columns (view)
+  Vk.shape[1] = k;
+  Tensor up = einsum(c, "ik,ia->ka", Uk, left);
+  Tensor dn = einsum(c, "ai,ik->ak", right, Vk);
+  up = scale_dim(c, up, 0, w);
+  dn = scale_dim(c, dn, 1, w);
+  Tensor sg = row_signs(c, up);
+  up = scale_dim(c, up, 0, sg);
+  dn = scale_dim(c, dn, 1, sg);
+  return ProjPair{up, dn, r.S};
+}
+
+// ------------------------------------------------------------------ frames
+Cell frame_transpose(Cell& cell) {
+  Cell o;
+  o.Lx = cell.Ly;
+  o.Ly = cell.Lx;
+  o.A.resize(cell.A.size());
+  o.env.resize(cell.env.size());
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      o.a(y, x) = cell.a(x, y).perm({0, 2, 1, 4, 3});
+      SiteEnv& e = cell.e(x, y);
+      SiteEnv& n = o.e(y, x);
+      n[C1] = e[C1].rev();  n[T1k] = e[T4k].rev(); n[T1b] = e[T4b].rev();
+      n[C2] = e[C4].rev();  n[T2k] = e[T3k].rev(); n[T2b] = e[T3b].rev();
+      n[C3] = e[C3].rev();  n[T3b] = e[T2b].rev(); n[T3k] = e[T2k].rev();
+      n[C4] = e[C2].rev();  n[T4b] = e[T1b].rev(); n[T4k] = e[T1k].rev();
+    }
+  return o;
+}
+
+// 180 degree rotation with the ket and bra layers relabelled (real A): edges and
+// C2/C4 keep their leg order; C1 is stored [next, previous] and C3 [previous,
+// next] along the chain, so these two are transposed when they trade places.
+Cell frame_rot180(Cell& cell) {
+  Cell o;
+  o.Lx = cell.Lx;
+  o.Ly = cell.Ly;
+  o.A.resize(cell.A.size());
+  o.env.resize(cell.env.size());
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      o.a(-x, -y) = cell.a(x, y).perm({0, 3, 4, 1, 2});
+      SiteEnv& e = cell.e(x, y);
+      SiteEnv& n = o.e(-x, -y);
+      n[C1] = e[C3].rev(); n[T1k] = e[T3b]; n[T1b] = e[T3k];
+      n[C2] = e[C4];       n[T2k] = e[T4b]; n[T2b] = e[T4k];
+      n[C3] = e[C1].rev(); n[T3b] = e[T1k]; n[T3k] = e[T1b];
+      n[C4] = e[C2];       n[T4b] = e[T2k]; n[T4k] = e[T2b];
+    }
+  return o;
+}
+
+// ------------------------------------------------------------------ rho networks
+static Tensor mat(const Tensor& t, int nrow_dims) {
+  long long r = 1, cc = 1;
+  for (int i = 0; i < t.nd; ++i) (i < nrow_dims ? r : cc) *= t.shape[i];
+  return t.reshape({(int)r, (int)cc});
+}
+
+// Fig. 3a, upper box: the site's network above the cut under its bra row.
+// Open (T4b.n, A.d | A'.d', T2b.g).
+static Tensor green_rhoT(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor L = einsum(c, "ab,qlb->aql", E[C1], E[T4k]);
+  L = einsum(c, "aql,aui->qlui", L, E[T1k]);
+  L = einsum(c, "qlui,sulkr->qiskr", L, A);
+  Tensor R = einsum(c, "cf,frj->crj", E[C2], E[T2k]);
+  R = einsum(c, "iwc,crj->iwrj", E[T1b], R);
+  Tensor X = einsum(c, "qiskr,iwrj->qskwj", L, R);
+  X = einsum(c, "qskwj,nvq->skwjnv", X, E[T4b]);
+  X = einsum(c, "skwjnv,swvez->kjnez", X, A);
+  return mat(einsum(c, "kjnez,jzg->nkeg", X, E[T2b]), 2);
+}
+
+// Fig. 3a, lower box (site below the cut).  Rows (A'.u', T2k.f), cols (T4k.b, A.u).
+static Tensor green_rhoB(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor Y = einsum(c, "mn,kdm->nkd", E[C4], E[T3k]);
+  Y = einsum(c, "nkd,nvq->kdvq", Y, E[T4b]);
+  Tensor Z = einsum(c, "gh,hek->gek", E[C3], E[T3b]);
+  Z = einsum(c, "jzg,gek->jzek", E[T2b], Z);
+  Y = einsum(c, "kdvq,jzek->dvqjze", Y, Z);
+  Y = einsum(c, "dvqjze,swvez->dqjsw", Y, A);
+  Y = einsum(c, "dqjsw,qlb->djswlb", Y, E[T4k]);
+  Y = einsum(c, "djswlb,suldr->jwbur", Y, A);
+  return mat(einsum(c, "jwbur,frj->wfbu", Y, E[T2k]), 2);
+}
+
+// Upper part C1 T1k T4k A T1b C2 of the site, legs [q, s, k, r, w, f]
+static Tensor upper_ket_row(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor L = einsum(c, "ab,qlb->aql", E[C1], E[T4k]);
+  L = einsum(c, "aql,aui->qlui", L, E[T1k]);
+  L = einsum(c, "qlui,sulkr->qiskr", L, A);
+  Tensor R = einsum(c, "iwc,cf->iwf", E[T1b], E[C2]);
+  return einsum(c, "qiskr,iwf->qskrwf", L, R);
+}
+
+// Fig. 8 upper box.  Rows (T4k.q, A.d), cols (A.s, T1b.u', T2k.j).
+static Tensor yellow_rhoT(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor X = upper_ket_row(c, E, A);
+  return mat(einsum(c, "qskrwf,frj->qkswj", X, E[T2k]), 2);
+}
+
+// Fig. 8 lower box.  Rows (A'.s, A'.u', T2b.j), cols (T4b.q, T3k.d).
+static Tensor yellow_rhoB(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor Y = einsum(c, "mn,kdm->nkd", E[C4], E[T3k]);
+  Y = einsum(c, "nkd,nvq->kdvq", Y, E[T4b]);
+  Tensor Z = einsum(c, "gh,hek->gek", E[C3], E[T3b]);
+  Z = einsum(c, "jzg,gek->jzek", E[T2b], Z);
+  Y = einsum(c, "kdvq,jzek->dvqjze", Y, Z);
+  Y = einsum(c, "dvqjze,swvez->swjqd", Y, A);
+  return mat(Y, 3);
+}
+
+// Eqs. (splitCTMRG_*), ket layer: absorb A and apply green (E-cut) and yellow
+// (I-cut) projectors.  ga = green pair of the band above the site, gb = below.
+static KetStage ket_stage(Ctx& c, SiteEnv& E, const Tensor& A, const ProjPair& ga, const ProjPair& y,
+                          const ProjPair& gb) {
+  KetStage K;
+  Tensor X = einsum(c, "ab,aui->bui", E[C1], E[T1k]);
+  K.C1k = einsum(c, "bui,gbu->ig", X, ga.up);
+  Tensor Z = einsum(c, "bug,qlb->ugql", ga.dn, E[T4k]);
+  Z = einsum(c, "ugql,suldr->gqsdr", Z, A);
+  K.T4kk = einsum(c, "gqsdr,yqd->grys", Z, y.up);
+  Z = einsum(c, "qky,nvq->kynv", y.dn, E[T4b]);
+  K.T4bk = einsum(c, "kynv,tnk->yvt", Z, gb.up);
+  Z = einsum(c, "mn,kdm->nkd", E[C4], E[T3k]);
+  K.C4k = einsum(c, "nkd,ndt->tk", Z, gb.dn);
+  return K;
+}
+
+// column y of the upper 2x2 half after the ket stage: [r, c, t, e, z]
+static Tensor upper_left_k(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K) {
+  Tensor X = einsum(c, "ig,grys->irys", K.C1k, K.T4kk);
+  X = einsum(c, "irys,iwc->ryswc", X, E[T1b]);
+  X = einsum(c, "ryswc,yvt->rswcvt", X, K.T4bk);
+  return einsum(c, "rswcvt,swvez->rctez", X, A);
+}
+
+// column y+1 of the upper half (site (x, y+1)): [c, l, v, D, E, g]
+static Tensor upper_right(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor Y = einsum(c, "cui,iwC->cuwC", E[T1k], E[T1b]);
+  Y = einsum(c, "cuwC,Cf->cuwf", Y, E[C2]);
+  Y = einsum(c, "cuwf,fRj->cuwRj", Y, E[T2k]);
+  Y = einsum(c, "cuwRj,jZg->cuwRZg", Y, E[T2b]);
+  Y = einsum(c, "cuwRZg,SulDR->cwZgSlD", Y, A);
+  return einsum(c, "cwZgSlD,SwvEZ->clvDEg", Y, A);
+}
+
+// column y of the lower half after the ket stage: [h, w, z, g, r]
+static Tensor lower_left_k(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K) {
+  Tensor Z = einsum(c, "tk,hek->the", K.C4k, E[T3b]);
+  Z = einsum(c, "the,yvt->heyv", Z, K.T4bk);
+  Z = einsum(c, "heyv,swvez->hyswz", Z, A);
+  return einsum(c, "hyswz,grys->hwzgr", Z, K.T4kk);
+}
+
+// column y+1 of the lower half (site (x+1, y+1)): [U, W, f, h, l, v]
+static Tensor lower_right(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor W = einsum(c, "fRj,jZG->fRZG", E[T2k], E[T2b]);
+  W = einsum(c, "fRZG,GH->fRZH", W, E[C3]);
+  W = einsum(c, "fRZH,HEK->fRZEK", W, E[T3b]);
+  W = einsum(c, "fRZEK,KDh->fRZEDh", W, E[T3k]);
+  W = einsum(c, "fRZEDh,SUlDR->fZEhSUl", W, A);
+  return einsum(c, "fZEhSUl,SWvEZ->UWfhlv", W, A);
+}
+
+// teal (two-column reading): rows (T4b_k.t, A'.d'), cols (A.d, A'.d', T2b.g of y+1)
+static Tensor teal_rhoT(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K, SiteEnv& E2, const Tensor& A2) {
+  Tensor R = einsum(c, "rctez,crzDEg->teDEg", upper_left_k(c, E, A, K), upper_right(c, E2, A2));
+  return mat(R, 2);
+}
+
+static Tensor teal_rhoB(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K, SiteEnv& E2, const Tensor& A2) {
+  Tensor R = einsum(c, "UWfhlv,hwvgl->UWfgw", lower_right(c, E2, A2), lower_left_k(c, E, A, K));
+  return mat(R, 3);
+}
+
+// red (two-column reading): rows (T4k_k.y, T4k_k.s, T1b.u'), cols (A.d, A.s, T1b.u', T2k.j of y+1)
+static Tensor red_rhoT(Ctx& c, SiteEnv& E, const KetStage& K, SiteEnv& E2, const Tensor& A2) {
+  Tensor X = einsum(c, "ig,grys->irys", K.C1k, K.T4kk);
+  X = einsum(c, "irys,iwc->ryswc", X, E[T1b]);
+  Tensor Y = einsum(c, "cui,iWC->cuWC", E2[T1k], E2[T1b]);
+  Y = einsum(c, "cuWC,Cf->cuWf", Y, E2[C2]);
+  Y = einsum(c, "cuWf,fRj->cuWRj", Y, E2[T2k]);
+  Y = einsum(c, "cuWRj,SulDR->cWjSlD", Y, A2);
+  return mat(einsum(c, "ryswc,cWjSrD->yswDSWj", X, Y), 3);
+}
+
+static Tensor red_rhoB(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K, SiteEnv& E2, const Tensor& A2) {
+  Tensor Z = einsum(c, "tk,hek->the", K.C4k, E[T3b]);
+  Z = einsum(c, "the,yvt->heyv", Z, K.T4bk);
+  Z = einsum(c, "heyv,swvez->hyswz", Z, A);
+  Tensor W = einsum(c, "jZG,GH->jZH", E2[T2b], E2[C3]);
+  W = einsum(c, "jZH,HEK->jZEK", W, E2[T3b]);
+  W = einsum(c, "jZEK,KDh->jZEDh", W, E2[T3k]);
+  W = einsum(c, "jZEDh,SWvEZ->jDhSWv", W, A2);
+  return mat(einsum(c, "jDhSWv,hyswv->DSWjysw", W, Z), 4);
+}
+
+static ProjPair shaped(const ProjPair& p, int a0, int a1, int a2 = 0) {
+  ProjPair q = p;
+  int k = p.up.shape[0];
+  if (a2) {
+    q.up = p.up.reshape({k, a0, a1, a2});
+    q.dn = p.dn.reshape({a0, a1, a2, k});
+  } else {
+    q.up = p.up.reshape({k, a0, a1});
+    q.dn = p.dn.reshape({a0, a1, k});
+  }
+  return q;
+}
+
+// ------------------------------------------------------------------ left move
+void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& out) {
+  const int Lx = cell.Lx;
+  const int D = P.D, p = P.p, chi = P.chi;
+  out.g.resize(Lx); out.y.resize(Lx); out.t.resize(Lx); out.r.resize(Lx); out.K.resize(Lx);
+  for (int x = 0; x < Lx; ++x)
+    out.g[x] = shaped(projector(c, P, green_rhoT(c, cell.e(x, y), cell.a(x, y)),
+                                green_rhoB(c, cell.e(x + 1, y), cell.a(x + 1, y))), chi, D);
+  for (int x = 0; x < Lx; ++x)
+    out.y[x] = shaped(projector(c, P, yellow_rhoT(c, cell.e(x, y), cell.a(x, y)),
+                                yellow_rhoB(c, cell.e(x, y), cell.a(x, y))), chi, D);
+  for (int x = 0; x < Lx; ++x)
+    out.K[x] = ket_stage(c, cell.e(x, y), cell.a(x, y), out.g[(x + Lx - 1) % Lx], out.y[x], out.g[x]);
+  for (int x = 0; x < Lx; ++x) {
+    int xp = (x + 1) % Lx;
+    out.t[x] = shaped(projector(c, P, teal_rhoT(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1),
+                                                cell.a(x, y + 1)),
+                                teal_rhoB(c, cell.e(xp, y), cell.a(xp, y), out.K[xp], cell.e(xp, y + 1),
+                                          cell.a(xp, y + 1))), chi, D);
+  }
+  for (int x = 0; x < Lx; ++x)
+    out.r[x] = shaped(projector(c, P, red_rhoT(c, cell.e(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)),
+                                red_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1),
+                                         cell.a(x, y + 1))), chi, p, D);
+}
+
+void left_move(Ctx& c, const Params& P, Cell& cell) {
+  const int Lx = cell.Lx, Ly = cell.Ly;
+  for (int y = 0; y < Ly; ++y) {
+    ColumnProj cp;
+    column_projectors(c, P, cell, y, cp);
+    std::vector<KetStage>& K = cp.K;
+    std::vector<ProjPair>& t = cp.t;
+    std::vector<ProjPair>& r = cp.r;
+    // bra layer: absorb A' and apply teal (E-cut) and red (I-cut) projectors
+    std::vector<std::array<Tensor, 4>> out(Lx);
+    for (int x = 0; x < Lx; ++x) {
+      SiteEnv& E = cell.e(x, y);
+      const Tensor& A = cell.a(x, y);
+      const ProjPair& ta = t[(x + Lx - 1) % Lx];
+      const ProjPair& tb = t[x];
+      Tensor X = einsum(c, "ig,iwc->gwc", K[x].C1k, E[T1b]);
+      Tensor nC1 = einsum(c, "gwc,Tgw->cT", X, ta.up);
+      Tensor Z = einsum(c, "gwT,grys->Twrys", ta.dn, K[x].T4kk);
+      Tensor nT4k = einsum(c, "Twrys,Pysw->PrT", Z, r[x].up);
+      Z = einsum(c, "yswP,yvt->swPvt", r[x].dn, K[x].T4bk);
+      Z = einsum(c, "swPvt,swvez->Ptez", Z, A);
+      Tensor nT4b = einsum(c, "Ptez,Ote->OzP", Z, tb.up);
+      Z = einsum(c, "tk,hek->the", K[x].C4k, E[T3b]);
+      Tensor nC4 = einsum(c, "the,teO->hO", Z, tb.dn);
+      out[x] = {rescale(c, nC1), rescale(c, nT4k), rescale(c, nT4b), rescale(c, nC4)};
+    }
+    for (int x = 0; x < Lx; ++x) {
+      SiteEnv& e = cell.e(x, y + 1);
+      e[C1] = out[x][0];
+      e[T4k] = out[x][1];
+      e[T4b] = out[x][2];
+      e[C4] = out[x][3];
+    }
+  }
+}
+
+void move(Ctx& c, const Params& P, Cell& cell, int dir) {
+  if (dir == 0) {
+    left_move(c, P, cell);
+  } else if (dir == 1) {
+    Cell t = frame_transpose(cell);
+    Params q = P;
+    std::swap(q.Lx, q.Ly);
+    left_move(c, q, t);
+    cell.env = frame_transpose(t).env;
+  } else if (dir == 2) {
+    Cell t = frame_rot180(cell);
+    left_move(c, P, t);
+    cell.env = frame_rot180(t).env;
+  } else if (dir == 3) {
+    Cell t = frame_rot180(cell);
+    Cell u = frame_transpose(t);
+    Params q = P;
+    std::swap(q.Lx, q.Ly);
+    left_move(c, q, u);
+    t.env = frame_transpose(u).env;
+    cell.env = frame_rot180(t).env;
+  } else {
+    throw ArgError("direction must be 0..3");
+  }
+}
+
+// ------------------------------------------------------------------ init
+// Split a conventional edge T[P,K,K2,N] (matrix (P K) x (K2 N)) into
+// first[P,K,i] = U sqrt(S) and second[i,K2,N] = sqrt(S) V^T, keeping
+// min(chi, rank) values above the cutoff, sign fixed on the columns of U,
+// zero-padded to [chi_P, K, chi] and [chi, K2, chi_N].
+static void split_edge(Ctx& c, const Params& P, const Tensor& T, Tensor& first, Tensor& second, int padP, int padN) {
+  const int Pd = T.shape[0], Kd = T.shape[1], K2 = T.shape[2], Nd = T.shape[3];
+  const int rows = Pd * Kd, cols = K2 * Nd;
+  SCTM_CHECK(rows == cols, "edge split expects a square matrix");
+  Tensor M = T.reshape({rows, cols});
+  SVDResult r = svd(c, M, P.eps_l);
+  const int k = std::min(P.chi, rows);
+  Tensor q = spectrum_map(c, r.S, k, P.cutoff, 1);
+  Tensor Uk = r.U, Vk = r.V;
+  Uk.shape[1] = k;
+  Vk.shape[1] = k;
+  Tensor sg = row_signs(c, Uk.rev());     // sign of each U column
+  Tensor Us = scale_dim(c, scale_dim(c, Uk, 1, q), 1, sg);
+  Tensor Vs = scale_dim(c, scale_dim(c, Vk, 1, q), 1, sg);
+  first = c.zeros({padP, Kd, P.chi});
+  second = c.zeros({P.chi, K2, padN});
+  Tensor fv = first, sv = second;
+  fv.shape[0] = Pd; fv.shape[2] = k;
+  sv.shape[0] = k;  sv.shape[2] = Nd;
+  copy_into(c, Us.reshape({Pd, Kd, k}), fv);
+  copy_into(c, copy(c, Vs.rev()).reshape({k, K2, Nd}), sv);
+}
+
+void init_env(Ctx& c, const Params& P, Cell& cell) {
+  const int D = P.D, D2 = D * D, chi = P.chi;
+  SCTM_CHECK(D2 <= chi, "chi must be at least D^2 (initial corner dimension)");
+  struct Pieces { Tensor c1, t1, c2, t2, c3, t3, c4, t4; };
+  std::vector<Pieces> pc(cell.Lx * cell.Ly);
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      const Tensor& A = cell.a(x, y);
+      Pieces& q = pc[x * cell.Ly + y];
+      q.c1 = einsum(c, "suldr,sulez->rzde", A, A).reshape({D2, D2});
+      q.t1 = einsum(c, "suldr,suvez->lvderz", A, A).reshape({D2, D, D, D2});
+      q.c2 = einsum(c, "suldr,suver->lvde", A, A).reshape({D2, D2});
+      q.t2 = einsum(c, "suldr,swver->uwlvde", A, A).reshape({D2, D, D, D2});
+      q.c3 = einsum(c, "suldr,swvdr->uwlv", A, A).reshape({D2, D2});
+      q.t3 = einsum(c, "suldr,swvdz->rzwulv", A, A).reshape({D2, D, D, D2});
+      q.c4 = einsum(c, "suldr,swldz->rzuw", A, A).reshape({D2, D2});
+      q.t4 = einsum(c, "suldr,swlez->dezruw", A, A).reshape({D2, D, D, D2});
+    }
+  auto P_ = [&](int x, int y) -> Pieces& {
+    x = (x % cell.Lx + cell.Lx) % cell.Lx;
+    y = (y % cell.Ly + cell.Ly) % cell.Ly;
+    return pc[x * cell.Ly + y];
+  };
+  auto padC = [&](const Tensor& m) {
+    Tensor z = c.zeros({chi, chi});
+    Tensor v = z;
+    v.shape[0] = D2;
+    v.shape[1] = D2;
+    copy_into(c, m, v);
+    return z;
+  };
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      SiteEnv& e = cell.e(x, y);
+      e[C1] = padC(P_(x - 1, y - 1).c1);
+      e[C2] = padC(P_(x - 1, y + 1).c2);
+      e[C3] = padC(P_(x + 1, y + 1).c3);
+      e[C4] = padC(P_(x + 1, y - 1).c4);
+      split_edge(c, P, P_(x - 1, y).t1, e[T1k], e[T1b], chi, chi);
+      split_edge(c, P, P_(x, y + 1).t2, e[T2k], e[T2b], chi, chi);
+      split_edge(c, P, P_(x + 1, y).t3, e[T3b], e[T3k], chi, chi);
+      split_edge(c, P, P_(x, y - 1).t4, e[T4b], e[T4k], chi, chi);
+    }
+}
+
+// ------------------------------------------------------------------ energy
+// Two-site operators h[(t_i t_j), (s_i s_j)] are decomposed on the host into
+// sum_k O_k (x) Q_k (operator Schmidt decomposition of a p^2 x p^2 matrix); the
+// 2x2 patch is contracted as four enlarged corners with the ket of a corner
+// replaced by O.A.  Bond value = <H_top(o1,o2), H_bot(o3,o4)> / <H_top(I,I), H_bot(I,I)>.
+static void host_svd(int n, std::vector<double> a, std::vector<double>& U, std::vector<double>& S,
+                     std::vector<double>& V) {
+  // one-sided Jacobi on an n x n host matrix (bond operator, n = p^2)
+  V.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    bool rot = false;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        double al = 0, be = 0, ga = 0;
+        for (int e = 0; e < n; ++e) al += a[e * n + i] * a[e * n + i], be += a[e * n + j] * a[e * n + j],
+                                    ga += a[e * n + i] * a[e * n + j];
+        if (std::fabs(ga) <= 1e-15 * std::sqrt(al * be) || ga == 0) continue;
+        rot = true;
+        double z = (be - al) / (2 * ga);
+        double t = (z >= 0 ? 1.0 : -1.0) / (std::fabs(z) + std::sqrt(1 + z * z));
+        double cs = 1 / std::sqrt(1 + t * t), sn = cs * t;
+        for (int e = 0; e < n; ++e) {
+          double x = a[e * n + i], y = a[e * n + j];
+          a[e * n + i] = cs * x - sn * y, a[e * n + j] = sn * x + cs * y;
+          double vx = V[e * n + i], vy = V[e * n + j];
+          V[e * n + i] = cs * vx - sn * vy, V[e * n + j] = sn * vx + cs * vy;
+        }
+      }
+    if (!rot) break;
+  }
+  S.assign(n, 0.0);
+  U.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double s = 0;
+    for (int e = 0; e < n; ++e) s += a[e * n + i] * a[e * n + i];
+    S[i] = std::sqrt(s);
+    for (int e = 0; e < n; ++e) U[e * n + i] = S[i] > 0 ? a[e * n + i] / S[i] : 0;
+  }
+}
+
+struct OpTerm {
+  std::vector<double> O, Q;   // p x p each, O[t*p+s]
+};
+
+static std::vector<OpTerm> decompose(int p, const double* h) {
+  std::vector<OpTerm> out;
+  if (!h) return out;
+  const int n = p * p;
+  // X[(t_i s_i), (t_j s_j)] = h[(t_i t_j), (s_i s_j)]
+  std::vector<double> X(n * n);
+  for (int ti = 0; ti < p; ++ti)
+    for (int tj = 0; tj < p; ++tj)
+      for (int si = 0; si < p; ++si)
+        for (int sj = 0; sj < p; ++sj)
+          X[(ti * p + si) * n + (tj * p + sj)] = h[(ti * p + tj) * n + (si * p + sj)];
+  std::vector<double> U, S, V;
+  host_svd(n, X, U, S, V);
+  double smax = 0;
+  for (double s : S) smax = std::max(smax, s);
+  for (int k = 0; k < n; ++k) {
+    if (S[k] <= 1e-14 * smax) continue;
+    OpTerm t;
+    t.O.resize(n);
+    t.Q.resize(n);
+    for (int r = 0; r < n; ++r) t.O[r] = U[r * n + k] * S[k], t.Q[r] = V[r * n + k];
+    out.push_back(t);
+  }
+  return out;
+}
+
+static Tensor fuse_edge(Ctx& c, const Tensor& a, const Tensor& b, const char* spec) { return einsum(c, spec, a, b); }
+
+// enlarged corners (conventional edges), ket = Ak, bra = A
+static Tensor corner_TL(Ctx& c, const Tensor& C1t, const Tensor& T1, const Tensor& T4, const Tensor& Ak, const Tensor& A) {
+  Tensor X = einsum(c, "ab,auwc->buwc", C1t, T1);
+  X = einsum(c, "buwc,nvlb->uwcnvl", X, T4);
+  X = einsum(c, "uwcnvl,suldr->wcnvsdr", X, Ak);
+  return mat(einsum(c, "wcnvsdr,swvez->crznde", X, A), 3);   // [(c,r,z), (n,d,e)]
+}
+static Tensor corner_TR(Ctx& c, const Tensor& T1, const Tensor& C2t, const Tensor& T2, const Tensor& Ak, const Tensor& A) {
+  Tensor Y = einsum(c, "auwc,cf->auwf", T1, C2t);
+  Y = einsum(c, "auwf,frzg->auwrzg", Y, T2);
+  Y = einsum(c, "auwrzg,suldr->awzgsld", Y, Ak);
+  return mat(einsum(c, "awzgsld,swvez->alvdeg", Y, A), 3);   // [(a,l,v), (d,e,g)]
+}
+static Tensor corner_BR(Ctx& c, const Tensor& T2, const Tensor& C3t, const Tensor& T3, const Tensor& Ak, const Tensor& A) {
+  Tensor Z = einsum(c, "frzg,gh->frzh", T2, C3t);
+  Z = einsum(c, "frzh,hedm->frzedm", Z, T3);
+  Z = einsum(c, "frzedm,suldr->fzemsul", Z, Ak);
+  return mat(einsum(c, "fzemsul,swvez->uwflvm", Z, A), 3);   // [(u,w,f), (l,v,m)]
+}
+static Tensor corner_BL(Ctx& c, const Tensor& T4, const Tensor& C4t, const Tensor& T3, const Tensor& Ak, const Tensor& A) {
+  Tensor W = einsum(c, "hedm,mn->hedn", T3, C4t);
+  W = einsum(c, "hedn,nvlb->hedvlb", W, T4);
+  W = einsum(c, "hedvlb,suldr->hevbsur", W, Ak);
+  return mat(einsum(c, "hevbsur,swvez->buwrzh", W, A), 3);   // [(b,u,w), (r,z,h)]
+}
+
+std::vector<EnergyTerm> energy_terms(Ctx& c, const Params& P, Cell& cell, const double* h_nn,
+                                     const double* h_diag) {
+  const int p = P.p;
+  std::vector<OpTerm> tn = decompose(p, h_nn), td = decompose(p, h_diag);
+  // operator list: index 0 = identity
+  std::vector<std::vector<double>> ops;
+  std::vector<double> I(p * p, 0.0);
+  for (int i = 0; i < p; ++i) I[i * p + i] = 1.0;
+  ops.push_back(I);
+  struct Bond { int o1, o2; };   // indices into ops
+  std::vector<std::pair<int, int>> nnp, dgp;
+  for (auto& t : tn) {
+    ops.push_back(t.O); int a = (int)ops.size() - 1;
+    ops.push_back(t.Q); int b = (int)ops.size() - 1;
+    nnp.push_back({a, b});
+  }
+  for (auto& t : td) {
+    ops.push_back(t.O); int a = (int)ops.size() - 1;
+    ops.push_back(t.Q); int b = (int)ops.size() - 1;
+    dgp.push_back({a, b});
+  }
+  std::vector<Tensor> opd(ops.size());
+  for (size_t i = 0; i < ops.size(); ++i) {
+    bool t = c.tape.active;
+    c.tape.active = false;
+    opd[i] = from_host(c, {p, p}, ops[i].data());
+    c.tape.active = t;
+  }
+  std::vector<EnergyTerm> terms;
+  const double inv_n = 1.0 / (cell.Lx * cell.Ly);
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      SiteEnv& eTL = cell.e(x, y);
+      SiteEnv& eTR = cell.e(x, y + 1);
+      SiteEnv& eBR = cell.e(x + 1, y + 1);
+      SiteEnv& eBL = cell.e(x + 1, y);
+      Tensor T1L = fuse_edge(c, eTL[T1k], eTL[T1b], "aui,iwc->auwc");
+      Tensor T4T = fuse_edge(c, eTL[T4b], eTL[T4k], "nvq,qlb->nvlb");
+      Tensor T1R = fuse_edge(c, eTR[T1k], eTR[T1b], "aui,iwc->auwc");
+      Tensor T2T = fuse_edge(c, eTR[T2k], eTR[T2b], "frj,jzg->frzg");
+      Tensor T2B = fuse_edge(c, eBR[T2k], eBR[T2b], "frj,jzg->frzg");
+      Tensor T3R = fuse_edge(c, eBR[T3b], eBR[T3k], "hek,kdm->hedm");
+      Tensor T3L = fuse_edge(c, eBL[T3b], eBL[T3k], "hek,kdm->hedm");
+      Tensor T4B = fuse_edge(c, eBL[T4b], eBL[T4k], "nvq,qlb->nvlb");
+      const Tensor& aTL = cell.a(x, y);
+      const Tensor& aTR = cell.a(x, y + 1);
+      const Tensor& aBR = cell.a(x + 1, y + 1);
+      const Tensor& aBL = cell.a(x + 1, y);
+      std::vector<Tensor> cTL(ops.size()), cTR(ops.size()), cBR(ops.size()), cBL(ops.size());
+      auto kTL = [&](int o) -> Tensor& {
+        if (!cTL[o].data) cTL[o] = corner_TL(c, eTL[C1], T1L, T4T, o ? einsum(c, "ts,suldr->tuldr", opd[o], aTL) : aTL, aTL);
+        return cTL[o];
+      };
+      auto kTR = [&](int o) -> Tensor& {
+        if (!cTR[o].data) cTR[o] = corner_TR(c, T1R, eTR[C2], T2T, o ? einsum(c, "ts,suldr->tuldr", opd[o], aTR) : aTR, aTR);
+        return cTR[o];
+      };
+      auto kBR = [&](int o) -> Tensor& {
+        if (!cBR[o].data) cBR[o] = corner_BR(c, T2B, eBR[C3], T3R, o ? einsum(c, "ts,suldr->tuldr", opd[o], aBR) : aBR, aBR);
+        return cBR[o];
+      };
+      auto kBL = [&](int o) -> Tensor& {
+        if (!cBL[o].data) cBL[o] = corner_BL(c, T4B, eBL[C4], T3L, o ? einsum(c, "ts,suldr->tuldr", opd[o], aBL) : aBL, aBL);
+        return cBL[o];
+      };
+      std::map<std::pair<int, int>, Tensor> top, bot;
+      auto Htop = [&](int o1, int o2) -> Tensor& {
+        auto key = std::make_pair(o1, o2);
+        if (!top.count(key)) top[key] = einsum(c, "ra,rb->ab", kTL(o1), kTR(o2));
+        return top[key];
+      };
+      auto Hbot = [&](int o3, int o4) -> Tensor& {
+        auto key = std::make_pair(o3, o4);
+        if (!bot.count(key)) bot[key] = einsum(c, "al,bl->ab", kBL(o3), kBR(o4));
+        return bot[key];
+      };
+      Tensor den = dot(c, Htop(0, 0), Hbot(0, 0));
+      // nearest-neighbour bonds, half weight each (every bond lies in two patches)
+      for (auto& pr : nnp) {
+        int o = pr.first, q = pr.second;
+        terms.push_back({dot(c, Htop(o, q), Hbot(0, 0)), den, 0.5 * inv_n});   // top    (TL, TR)
+        terms.push_back({dot(c, Htop(0, 0), Hbot(o, q)), den, 0.5 * inv_n});   // bottom (BL, BR)
+        terms.push_back({dot(c, Htop(o, 0), Hbot(q, 0)), den, 0.5 * inv_n});   // left   (TL, BL)
+        terms.push_back({dot(c, Htop(0, o), Hbot(0, q)), den, 0.5 * inv_n});   // right  (TR, BR)
+      }
+      for (auto& pr : dgp) {
+        int o = pr.first, q = pr.second;
+        terms.push_back({dot(c, Htop(o, 0), Hbot(0, q)), den, inv_n});         // TL - BR
+        terms.push_back({dot(c, Htop(0, o), Hbot(q, 0)), den, inv_n});         // TR - BL
+      }
+    }
+  return terms;
+}
+
+}  // namespace sctm

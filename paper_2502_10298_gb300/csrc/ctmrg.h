@@ -1,0 +1,74 @@
+// Split-CTMRG engine on one GPU: environment, directional moves, projectors,
+// 2x2-patch energy and the reverse pass.
+#pragma once
+#include <array>
+#include <vector>
+
+#include "ops.h"
+
+namespace sctm {
+
+enum Key { C1, T1k, T1b, C2, T2k, T2b, C3, T3b, T3k, C4, T4b, T4k, NKEY };
+
+// Environment of one site (Fig. 2).  Leg order of every tensor:
+//   C1[a,b] a->T1k b->T4k;  C2[c,f]  C3[g,h]  C4[m,n]  ([previous, next] along
+//   the clockwise chain for C2..C4, [next, previous] for C1);
+//   T1k[a,u,i] T1b[i,u',c] T2k[f,r,j] T2b[j,r',g] T3b[h,d',k] T3k[k,d,m]
+//   T4b[n,l',q] T4k[q,l,b]  ([previous, PEPS leg, next]).
+using SiteEnv = std::array<Tensor, NKEY>;
+
+struct Cell {
+  int Lx = 0, Ly = 0;
+  std::vector<Tensor> A;      // A[x*Ly + y] : [p, D, D, D, D]  (u, l, d, r)
+  std::vector<SiteEnv> env;   // env[x*Ly + y]
+  Tensor& a(int x, int y) { return A[((x % Lx + Lx) % Lx) * Ly + ((y % Ly + Ly) % Ly)]; }
+  SiteEnv& e(int x, int y) { return env[((x % Lx + Lx) % Lx) * Ly + ((y % Ly + Ly) % Ly)]; }
+};
+
+struct Params {
+  int Lx = 1, Ly = 1, p = 2, D = 2, chi = 16;
+  double cutoff = 1e-8;       // relative cutoff on the projector singular values
+  double gram_cutoff = 1e-15; // relative cutoff on Gram eigenvalues (reduction)
+  double eps_l = 1e-36;       // Lorentzian broadening (relative to s_max^4)
+};
+
+struct ProjPair {
+  Tensor up, dn;   // up: [k, alpha...], dn: [alpha..., k]
+  Tensor s;        // singular values of the decomposed core
+};
+
+// Projector pair from rhoT (alpha x beta) and rhoB (beta x alpha).
+ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB);
+
+struct KetStage {
+  Tensor C1k, T4kk, T4bk, C4k;   // C1k[i,g] T4kk[g,r,y,s] T4bk[y,v,t] C4k[t,k]
+};
+
+// All projectors of one column of a left move (green, yellow, teal, red per
+// row) and the ket-stage tensors.
+struct ColumnProj {
+  std::vector<ProjPair> g, y, t, r;
+  std::vector<KetStage> K;
+};
+void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& out);
+
+Cell frame_transpose(Cell& cell);
+Cell frame_rot180(Cell& cell);
+
+// one left move in the canonical frame (all columns, in order)
+void left_move(Ctx& c, const Params& P, Cell& cell);
+// directional move: 0 left, 1 top, 2 right, 3 bottom
+void move(Ctx& c, const Params& P, Cell& cell, int dir);
+
+// environment from the neighbours' double layers, padded to chi
+void init_env(Ctx& c, const Params& P, Cell& cell);
+
+// per-site energy pieces: returns the list of (numerator, denominator, weight)
+struct EnergyTerm {
+  Tensor num, den;
+  double w;
+};
+std::vector<EnergyTerm> energy_terms(Ctx& c, const Params& P, Cell& cell, const double* h_nn,
+                                     const double* h_diag);
+
+}  // namespace sctm

@@ -1,0 +1,163 @@
+// Batched FP64 singular value decomposition by one-sided (Hestenes) Jacobi.
+//
+// Projectors need the full SVD M = U S V^T of square matrices (Sec. II.B);
+// the reverse pass needs all singular vectors.  One-sided Jacobi rotates pairs
+// of columns of W = M V until they are mutually orthogonal, then
+// S = column norms and U = W S^{-1}.  It is accurate in the relative sense
+// for small singular values, which matters because the projector divides by
+// sqrt(s).  Column pairs follow the round-robin tournament ordering, so the
+// n/2 rotations of a round are independent and run on separate warps.
+//
+// One CTA owns one matrix of the batch.  Small matrices (n <= kSmemN) live in
+// shared memory; larger ones in a global workspace (kept in L2).
+#include "common.h"
+#include "kernels.h"
+
+namespace sctm {
+
+constexpr int kSmemN = 48;   // 2 n^2 doubles <= 36 KiB of shared memory
+constexpr int kSvdThreads = 1024;
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Pair (i, j) of round r in the circle-method tournament over np (even) players.
+__device__ inline void tournament_pair(int np, int r, int k, int& i, int& j) {
+  if (k == 0) { i = r; j = np - 1; }
+  else {
+    int m = np - 1;
+    i = (r + k) % m;
+    j = (r - k + m) % m;
+  }
+}
+
+// W, V: n x n column-major (column c at W + c*ld).  Returns number of sweeps.
+__device__ int jacobi_core(int n, double* W, double* V, int ld, int max_sweeps, double tol, int* flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int np = n + (n & 1);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = warp; k < np / 2; k += nwarp) {
+        int i, j;
+        tournament_pair(np, r, k, i, j);
+        if (i >= n || j >= n) continue;
+        if (i > j) { int t = i; i = j; j = t; }
+        double* wi = W + (long long)i * ld;
+        double* wj = W + (long long)j * ld;
+        double a = 0, b = 0, g = 0;
+        for (int e = lane; e < n; e += 32) {
+          double x = wi[e], y = wj[e];
+          a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
+        }
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        if (g == 0.0 || fabs(g) <= tol * sqrt(a) * sqrt(b)) continue;
+        double zeta = (b - a) / (2.0 * g);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = c * t;
+        for (int e = lane; e < n; e += 32) {
+          double x = wi[e], y = wj[e];
+          wi[e] = c * x - s * y;
+          wj[e] = s * x + c * y;
+        }
+        double* vi = V + (long long)i * ld;
+        double* vj = V + (long long)j * ld;
+        for (int e = lane; e < n; e += 32) {
+          double x = vi[e], y = vj[e];
+          vi[e] = c * x - s * y;
+          vj[e] = s * x + c * y;
+        }
+        if (lane == 0) *flag = 1;
+      }
+      __syncthreads();
+    }
+    if (*flag == 0) break;
+    __syncthreads();
+  }
+  return sweep;
+}
+
+// M, U, V: batch of n x n row-major; S: batch of n.  work: batch * 2 * n * n doubles
+// (only used when n > kSmemN).  *status is set to -1 when a matrix did not converge.
+__global__ void __launch_bounds__(kSvdThreads)
+svd_kernel(int n, const double* __restrict__ M, double* __restrict__ U, double* __restrict__ S,
+           double* __restrict__ V, double* __restrict__ work, int* __restrict__ status,
+           int max_sweeps, double tol) {
+  extern __shared__ double sm[];
+  __shared__ int flag;
+  const long long nn = (long long)n * n;
+  const int b = blockIdx.x;
+  const double* Mb = M + b * nn;
+  double *W, *Vw;
+  if (n <= kSmemN) { W = sm; Vw = sm + nn; }
+  else { W = work + b * 2 * nn; Vw = W + nn; }
+  // W (column-major) = M;  V = identity
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+    int r = (int)(e / n), c = (int)(e % n);
+    W[(long long)c * n + r] = Mb[e];
+    Vw[(long long)c * n + r] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int sw = jacobi_core(n, W, Vw, n, max_sweeps, tol, &flag);
+  __syncthreads();
+  // singular values = column norms, then order by descending value
+  double* Sb = S + (long long)b * n;
+  for (int c = threadIdx.x >> 5; c < n; c += blockDim.x >> 5) {
+    double a = 0;
+    for (int e = threadIdx.x & 31; e < n; e += 32) a = fma(W[(long long)c * n + e], W[(long long)c * n + e], a);
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) Sb[c] = sqrt(a);   // unsorted for now
+  }
+  __syncthreads();
+  double* Ub = U + b * nn;
+  double* Vb = V + b * nn;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double sc = Sb[c];
+    int rank = 0;
+    for (int o = 0; o < n; ++o) {
+      double so = Sb[o];
+      rank += (so > sc) || (so == sc && o < c);
+    }
+    // rank-th column of the outputs
+    double inv = sc > 0 ? 1.0 / sc : 0.0;
+    for (int e = 0; e < n; ++e) {
+      Ub[(long long)e * n + rank] = W[(long long)c * n + e] * inv;
+      Vb[(long long)e * n + rank] = Vw[(long long)c * n + e];
+    }
+  }
+  __syncthreads();
+  // sort S in place: gather via ranks (second pass; values only)
+  if (threadIdx.x == 0 && sw >= max_sweeps) atomicExch(status, -1);   // sticky failure flag
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double sc = Sb[c];
+    int rank = 0;
+    for (int o = 0; o < n; ++o) {
+      double so = Sb[o];
+      rank += (so > sc) || (so == sc && o < c);
+    }
+    // stash sorted value in the workspace column slot of W (no longer needed)
+    W[rank] = sc;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) Sb[c] = W[c];
+}
+
+void launch_svd(int n, int batch, const double* M, double* U, double* S, double* V,
+                double* work, int* status, cudaStream_t s) {
+  if (batch == 0 || n == 0) return;
+  const int max_sweeps = 60;
+  const double tol = 2.3e-16 * 4.0 * sqrt((double)n);
+  size_t smem = (n <= kSmemN) ? (size_t)2 * n * n * sizeof(double) : 0;
+  svd_kernel<<<batch, kSvdThreads, smem, s>>>(n, M, U, S, V, work, status, max_sweeps, tol);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+size_t svd_work_doubles(int n, int batch) { return (n <= kSmemN) ? 0 : (size_t)batch * 2 * n * n; }
+
+}  // namespace sctm

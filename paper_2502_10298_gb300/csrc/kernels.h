@@ -1,0 +1,61 @@
+// Launch wrappers of the engine's CUDA kernels.
+#pragma once
+#include "common.h"
+
+namespace sctm {
+
+template <typename T>
+void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s);
+
+// Batched SVD of n x n row-major matrices: M = U diag(S) V^T, S descending.
+void launch_svd(int n, int batch, const double* M, double* U, double* S, double* V,
+                double* work, int* status, cudaStream_t s);
+size_t svd_work_doubles(int n, int batch);
+
+// out[g] = alpha * in[g] + beta * out[g] over one index group g (strides sa = in, sc = out).
+template <typename T>
+void launch_copy(const Group& g, T alpha, const T* in, T beta, T* out, cudaStream_t s);
+
+// X[b, i, j] *= (row ? v[b, i] : v[b, j]); X row-major (rows x cols), batch stride rows*cols.
+void launch_scale_rc(int batch, int rows, int cols, double* X, const double* v, int vstride, bool row,
+                     cudaStream_t s);
+
+// w[b, k] = f(S[b, k]) for k < kout, with cutoff relative to S[b, 0]:
+// mode 0: S^{-1/2} (0 below cutoff);  mode 1: S^{1/2} (0 below cutoff);
+// mode 2: 1 if kept else 0.
+void launch_spectrum_map(int batch, int n, int kout, const double* S, double* w, double cutoff,
+                         int mode, cudaStream_t s);
+
+// sgn[r] = sign of the largest-|.| entry of row r of a (rows x cols) matrix with
+// element (r, e) at P[r*rs + e*cs] (ties: first index).
+void launch_sign_find(int rows, int cols, const double* P, long long rs, long long cs, double* sgn,
+                      cudaStream_t s);
+
+// Reverse pass of the square SVD M = U S V^T (Lorentzian-broadened):
+// inner[i,j] = F_ij (J_ij - J_ji) s_j + d_ij Sbar_i + s_i F_ij (K_ij - K_ji),
+// F_ij = d / (d^2 + eps * s_max^4), d = s_j^2 - s_i^2.
+void launch_svd_adj_inner(int n, const double* S, const double* J, const double* K, const double* Sbar,
+                          double* inner, double eps, cudaStream_t s);
+
+// Sbar[k] += wbar[k] * f'(S[k]) for kept k (same modes and cutoff as launch_spectrum_map)
+void launch_spectrum_adj(int n, int kout, const double* S, const double* wbar, double* Sbar, double cutoff,
+                         int mode, cudaStream_t s);
+
+// Reverse pass of y = x / m, m = |x[k]| = max |x|:  xbar += ybar/m - e_k sign(x_k) (ybar.y)/m
+void launch_rescale_adj(long long n, const double* ybar, const double* y, const double* m,
+                        const long long* k, const double* xk_sign, const double* dot, double* xbar,
+                        cudaStream_t s);
+
+// Divide each tensor of a batch by its max |entry|; records the scale (and the
+// flat index of the maximum) for the reverse pass.
+void launch_rescale(int batch, long long n, double* X, long long stride, double* scale,
+                    long long* argmax, double* partial, cudaStream_t s);
+
+// out[b] = sum_i x[b, i] * y[b, i]  (deterministic tree reduction)
+void launch_dot(int batch, long long n, const double* x, const double* y, long long stride,
+                double* out, double* partial, cudaStream_t s);
+
+void launch_fill(long long n, double v, double* x, cudaStream_t s);
+void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s);
+
+}  // namespace sctm

@@ -1,0 +1,287 @@
+// Small memory-bound kernels of the engine: strided copies, row/column
+// scaling, spectrum maps, sign fixing, max-abs rescaling and dot products.
+#include "common.h"
+#include "kernels.h"
+
+namespace sctm {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void copy_kernel(Group g, long long total, T alpha, const T* __restrict__ in, T beta,
+                            T* __restrict__ out) {
+  for (long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x; lin < total;
+       lin += (long long)gridDim.x * blockDim.x) {
+    long long oi = group_offset(g, g.sa, lin);
+    long long oo = group_offset(g, g.sc, lin);
+    T v = alpha * in[oi];
+    if (beta != T(0)) v += beta * out[oo];
+    out[oo] = v;
+  }
+}
+
+static unsigned grid_for(long long total) {
+  long long g = (total + kThreads - 1) / kThreads;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+template <typename T>
+void launch_copy(const Group& g, T alpha, const T* in, T beta, T* out, cudaStream_t s) {
+  long long total = g.total();
+  if (total == 0) return;
+  copy_kernel<T><<<grid_for(total), kThreads, 0, s>>>(g, total, alpha, in, beta, out);
+  SCTM_CUDA(cudaGetLastError());
+}
+template void launch_copy<double>(const Group&, double, const double*, double, double*, cudaStream_t);
+template void launch_copy<float>(const Group&, float, const float*, float, float*, cudaStream_t);
+
+__global__ void scale_rc_kernel(int batch, int rows, int cols, double* X, const double* v, int vstride,
+                                bool row) {
+  long long per = (long long)rows * cols, total = per * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long b = e / per, r = (e % per) / cols, c = e % cols;
+    X[e] *= v[b * vstride + (row ? r : c)];
+  }
+}
+
+void launch_scale_rc(int batch, int rows, int cols, double* X, const double* v, int vstride, bool row,
+                     cudaStream_t s) {
+  long long total = (long long)batch * rows * cols;
+  if (total == 0) return;
+  scale_rc_kernel<<<grid_for(total), kThreads, 0, s>>>(batch, rows, cols, X, v, vstride, row);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+__global__ void spectrum_map_kernel(int batch, int n, int kout, const double* S, double* w, double cutoff,
+                                    int mode) {
+  int total = batch * kout;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int b = e / kout, k = e % kout;
+    double s0 = S[(long long)b * n];
+    double sk = (k < n) ? S[(long long)b * n + k] : 0.0;
+    bool keep = (k < n) && (sk > cutoff * s0) && (s0 > 0);
+    double r = 0.0;
+    if (keep) r = (mode == 0) ? 1.0 / sqrt(sk) : (mode == 1 ? sqrt(sk) : 1.0);
+    w[e] = r;
+  }
+}
+
+void launch_spectrum_map(int batch, int n, int kout, const double* S, double* w, double cutoff, int mode,
+                         cudaStream_t s) {
+  if (batch * kout == 0) return;
+  spectrum_map_kernel<<<grid_for(batch * kout), kThreads, 0, s>>>(batch, n, kout, S, w, cutoff, mode);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// one warp per row
+__global__ void sign_find_kernel(int rows, int cols, const double* P, long long rs, long long cs, double* sgn) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= rows) return;
+  const double* row = P + (long long)warp * rs;
+  double best = -1.0, val = 0.0;
+  int bi = 0x7fffffff;
+  for (int e = lane; e < cols; e += 32) {
+    double x = row[e * cs], ax = fabs(x);
+    if (ax > best || (ax == best && e < bi)) { best = ax; val = x; bi = e; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    double ov = __shfl_xor_sync(0xffffffffu, val, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; val = ov; bi = oi; }
+  }
+  if (lane == 0) sgn[warp] = (val < 0) ? -1.0 : 1.0;
+}
+
+void launch_sign_find(int rows, int cols, const double* P, long long rs, long long cs, double* sgn,
+                      cudaStream_t s) {
+  if (rows == 0) return;
+  long long threads = (long long)rows * 32;
+  sign_find_kernel<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, s>>>(rows, cols, P, rs, cs, sgn);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+__global__ void svd_adj_inner_kernel(int n, const double* S, const double* J, const double* K,
+                                     const double* Sbar, double* inner, double eps) {
+  double smax = S[0];
+  double e4 = eps * smax * smax * smax * smax;
+  long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    double v;
+    if (i == j) v = Sbar ? Sbar[i] : 0.0;
+    else {
+      double si = S[i], sj = S[j];
+      double d = sj * sj - si * si;
+      double F = d / (d * d + e4 + 1e-300);
+      double jj = J[(long long)i * n + j] - J[(long long)j * n + i];
+      double kk = K[(long long)i * n + j] - K[(long long)j * n + i];
+      v = F * jj * sj + si * F * kk;
+    }
+    inner[e] = v;
+  }
+}
+
+void launch_svd_adj_inner(int n, const double* S, const double* J, const double* K, const double* Sbar,
+                          double* inner, double eps, cudaStream_t s) {
+  long long total = (long long)n * n;
+  if (total == 0) return;
+  svd_adj_inner_kernel<<<grid_for(total), kThreads, 0, s>>>(n, S, J, K, Sbar, inner, eps);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+__global__ void spectrum_adj_kernel(int n, int kout, const double* S, const double* wbar, double* Sbar,
+                                    double cutoff, int mode) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kout || k >= n) return;
+  double s0 = S[0], sk = S[k];
+  bool keep = (sk > cutoff * s0) && (s0 > 0);
+  if (!keep || mode == 2) return;
+  double d = (mode == 0) ? -0.5 / (sk * sqrt(sk)) : 0.5 / sqrt(sk);
+  Sbar[k] += wbar[k] * d;
+}
+
+void launch_spectrum_adj(int n, int kout, const double* S, const double* wbar, double* Sbar, double cutoff,
+                         int mode, cudaStream_t s) {
+  if (kout == 0) return;
+  spectrum_adj_kernel<<<(kout + 255) / 256, 256, 0, s>>>(n, kout, S, wbar, Sbar, cutoff, mode);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+__global__ void rescale_adj_kernel(long long n, const double* ybar, const double* y, const double* m,
+                                   const long long* k, const double* xk_sign, const double* dot, double* xbar) {
+  double mm = *m;
+  if (mm <= 0) return;
+  double inv = 1.0 / mm;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double v = ybar[e] * inv;
+    if (e == *k) v -= (xk_sign ? *xk_sign : y[e]) * (*dot) * inv;
+    xbar[e] += v;
+  }
+}
+
+void launch_rescale_adj(long long n, const double* ybar, const double* y, const double* m, const long long* k,
+                        const double* xk_sign, const double* dot, double* xbar, cudaStream_t s) {
+  if (n == 0) return;
+  rescale_adj_kernel<<<grid_for(n), kThreads, 0, s>>>(n, ybar, y, m, k, xk_sign, dot, xbar);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// ---- max-abs rescale: two-level reduction (value, index) then scaling
+struct MaxIdx { double v; long long i; };
+
+__device__ inline MaxIdx better(MaxIdx a, MaxIdx b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+
+constexpr int kRedBlocks = 64;
+
+__global__ void maxabs_partial_kernel(long long n, const double* X, long long stride, double* partial) {
+  int b = blockIdx.y;
+  const double* x = X + b * stride;
+  MaxIdx m{-1.0, 0x7fffffffffffffffLL};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    m = better(m, MaxIdx{fabs(x[e]), e});
+  __shared__ double sv[kThreads];
+  __shared__ long long si[kThreads];
+  sv[threadIdx.x] = m.v; si[threadIdx.x] = m.i;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      MaxIdx r = better(MaxIdx{sv[threadIdx.x], si[threadIdx.x]}, MaxIdx{sv[threadIdx.x + o], si[threadIdx.x + o]});
+      sv[threadIdx.x] = r.v; si[threadIdx.x] = r.i;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[(b * kRedBlocks + blockIdx.x) * 2] = sv[0];
+    partial[(b * kRedBlocks + blockIdx.x) * 2 + 1] = (double)si[0];
+  }
+}
+
+__global__ void maxabs_final_scale_kernel(long long n, double* X, long long stride, const double* partial,
+                                          double* scale, long long* argmax) {
+  int b = blockIdx.x;
+  __shared__ double m;
+  __shared__ long long mi;
+  (void)mi;
+  if (threadIdx.x == 0) {
+    MaxIdx r{-1.0, 0x7fffffffffffffffLL};
+    for (int i = 0; i < kRedBlocks; ++i)
+      r = better(r, MaxIdx{partial[(b * kRedBlocks + i) * 2], (long long)partial[(b * kRedBlocks + i) * 2 + 1]});
+    m = r.v; mi = r.i;
+    scale[b] = r.v;
+    if (argmax) argmax[b] = r.i;
+  }
+  __syncthreads();
+  if (m <= 0) return;
+  double inv = 1.0 / m;
+  double* x = X + b * stride;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) x[e] *= inv;
+}
+
+void launch_rescale(int batch, long long n, double* X, long long stride, double* scale, long long* argmax,
+                    double* partial, cudaStream_t s) {
+  if (batch == 0 || n == 0) return;
+  maxabs_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, X, stride, partial);
+  SCTM_CUDA(cudaGetLastError());
+  maxabs_final_scale_kernel<<<batch, 1024, 0, s>>>(n, X, stride, partial, scale, argmax);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+__global__ void dot_partial_kernel(long long n, const double* x, const double* y, long long stride, double* partial) {
+  int b = blockIdx.y;
+  double acc = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[b * stride + e], y[b * stride + e], acc);
+  __shared__ double sv[kThreads];
+  sv[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sv[threadIdx.x] += sv[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[b * kRedBlocks + blockIdx.x] = sv[0];
+}
+
+__global__ void dot_final_kernel(int batch, const double* partial, double* out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double acc = 0;
+  for (int i = 0; i < kRedBlocks; ++i) acc += partial[b * kRedBlocks + i];
+  out[b] = acc;
+}
+
+void launch_dot(int batch, long long n, const double* x, const double* y, long long stride, double* out,
+                double* partial, cudaStream_t s) {
+  if (batch == 0) return;
+  dot_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, x, y, stride, partial);
+  SCTM_CUDA(cudaGetLastError());
+  dot_final_kernel<<<(batch + 127) / 128, 128, 0, s>>>(batch, partial, out);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+__global__ void fill_kernel(long long n, double v, double* x) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    x[e] = v;
+}
+__global__ void axpy_kernel(long long n, double a, const double* x, double* y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = fma(a, x[e], y[e]);
+}
+void launch_fill(long long n, double v, double* x, cudaStream_t s) {
+  if (n == 0) return;
+  fill_kernel<<<grid_for(n), kThreads, 0, s>>>(n, v, x);
+  SCTM_CUDA(cudaGetLastError());
+}
+void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s) {
+  if (n == 0) return;
+  axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+}  // namespace sctm

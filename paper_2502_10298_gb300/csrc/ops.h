@@ -1,0 +1,66 @@
+// Differentiable device operations of the engine.  Every op launches one of
+// the kernels of this directory and, while the tape is active, records the
+// closure that accumulates the adjoints of its inputs.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "tensor.h"
+
+namespace sctm {
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  Arena arena;
+  Tape tape;
+  double* partial = nullptr;     // reduction scratch (persistent)
+  int* svd_status = nullptr;     // per-call SVD sweep counts (persistent, device)
+  int svd_status_cap = 0;
+  bool svd_failed = false;
+
+  // new contiguous tensor of the given shape; gradient buffer (zeroed) when taping
+  Tensor empty(std::initializer_list<int> shape);
+  Tensor empty_shape(const int* shape, int nd);
+  Tensor zeros(std::initializer_list<int> shape);
+  Tensor scalar();
+  void zero_grad(const Tensor& t);
+  void ensure_grad(Tensor& t);
+};
+
+// C = alpha * einsum(spec, A, B) (+ beta * C when C is given and beta != 0).
+// spec like "ab,aui->bui"; an index may appear in A and/or B and/or C, but an
+// index of a single input must also be in C.
+Tensor einsum(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, double alpha = 1.0);
+void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, const Tensor& C,
+                 double alpha, double beta, bool record);
+
+// Full SVD of a square matrix (2-D, any strides): returns U, S, V with M = U S V^T.
+struct SVDResult {
+  Tensor U, S, V;
+};
+SVDResult svd(Ctx& c, const Tensor& M, double eps_l);
+
+// w[k] = f(S[k]) for k < kout with a cutoff relative to S[0] (see kernels.h modes)
+Tensor spectrum_map(Ctx& c, const Tensor& S, int kout, double cutoff, int mode);
+
+// Y = X scaled along `dim` by vector v (v may be a constant without gradient)
+Tensor scale_dim(Ctx& c, const Tensor& X, int dim, const Tensor& v);
+
+// Sign vector of a matrix: sign of the largest-|.| entry of each row (constant)
+Tensor row_signs(Ctx& c, const Tensor& P);
+
+// Contiguous copy of a view, or copy into an existing view (accumulating adjoints)
+Tensor copy(Ctx& c, const Tensor& X);
+void copy_into(Ctx& c, const Tensor& X, const Tensor& Y);
+
+// Y = X / max|X| (contiguous X)
+Tensor rescale(Ctx& c, const Tensor& X);
+
+// scalar = sum X .* Y over two equally shaped views (copied to contiguous)
+Tensor dot(Ctx& c, const Tensor& X, const Tensor& Y);
+
+Tensor from_host(Ctx& c, std::initializer_list<int> shape, const double* host);
+std::vector<double> to_host(Ctx& c, const Tensor& t);
+
+}  // namespace sctm
