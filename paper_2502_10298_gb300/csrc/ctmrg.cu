@@ -16,8 +16,10 @@ namespace sctm {
 // ------------------------------------------------------------------ projector
 // rhoT: alpha x beta (upper half), rhoB: beta x alpha (lower half).
 // M = rhoB rhoT has rank <= alpha; when alpha < beta both halves are reduced
-// first (App. A), here through their Gram matrices:
-//   rhoT rhoT^T = L_T L_T^T, rhoB^T rhoB = L_B L_B^T (eigendecompositions),
+// first (App. A: decompose rho^T and rho^B before multiplying them), here by
+// thin SVDs computed with one-sided Jacobi (relative accuracy):
+//   rhoT^T = Q_T S_T V_T^T -> rhoT = L_T Q_T^T with L_T = V_T S_T,
+//   rhoB   = Q_B S_B V_B^T -> rhoB = Q_B L_B^T with L_B = V_B S_B,
 //   K = L_B^T L_T = U S V^T,  P_up = S^-1/2 U^T L_B^T,  P_dn = L_T V S^-1/2,
 // which equals S^-1/2 U~^T rhoB and rhoT V~ S^-1/2 for the full M.
 ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB) {
@@ -25,14 +27,10 @@ ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rh
   SCTM_CHECK(rhoB.shape[0] == b && rhoB.shape[1] == a, "projector: rho shapes do not match");
   Tensor left, right;  // core = left @ right  (n x n), P_up = w U^T left, P_dn = right V w
   if (a < b) {
-    Tensor GT = einsum(c, "ab,cb->ac", rhoT, rhoT);
-    Tensor GB = einsum(c, "ba,bc->ac", rhoB, rhoB);
-    SVDResult eT = svd(c, GT, P.eps_l);
-    SVDResult eB = svd(c, GB, P.eps_l);
-    Tensor qT = spectrum_map(c, eT.S, a, P.gram_cutoff, 1);
-    Tensor qB = spectrum_map(c, eB.S, a, P.gram_cutoff, 1);
-    Tensor LT = scale_dim(c, eT.V, 1, qT);   // a x a
-    Tensor LB = scale_dim(c, eB.V, 1, qB);
+    SVDResult eT = svd(c, rhoT.rev(), P.eps_l);   // rhoT^T: b x a
+    SVDResult eB = svd(c, rhoB, P.eps_l);         // b x a
+    Tensor LT = scale_dim(c, eT.V, 1, eT.S);      // a x a
+    Tensor LB = scale_dim(c, eB.V, 1, eB.S);
     left = LB.rev();                         // L_B^T
     right = LT;
   } else {

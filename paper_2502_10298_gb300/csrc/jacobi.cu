@@ -15,7 +15,6 @@
 
 namespace sctm {
 
-constexpr int kSmemN = 48;   // 2 n^2 doubles <= 36 KiB of shared memory
 constexpr int kSvdThreads = 1024;
 
 __device__ inline double warp_sum(double v) {
@@ -33,8 +32,9 @@ __device__ inline void tournament_pair(int np, int r, int k, int& i, int& j) {
   }
 }
 
-// W, V: n x n column-major (column c at W + c*ld).  Returns number of sweeps.
-__device__ int jacobi_core(int n, double* W, double* V, int ld, int max_sweeps, double tol, int* flag) {
+// W: m x n column-major (column c at W + c*m), V: n x n column-major.
+// Returns the number of sweeps used.
+__device__ int jacobi_core(int m, int n, double* W, double* V, int max_sweeps, double tol, int* flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int np = n + (n & 1);
   int sweep = 0;
@@ -47,10 +47,10 @@ __device__ int jacobi_core(int n, double* W, double* V, int ld, int max_sweeps, 
         tournament_pair(np, r, k, i, j);
         if (i >= n || j >= n) continue;
         if (i > j) { int t = i; i = j; j = t; }
-        double* wi = W + (long long)i * ld;
-        double* wj = W + (long long)j * ld;
+        double* wi = W + (long long)i * m;
+        double* wj = W + (long long)j * m;
         double a = 0, b = 0, g = 0;
-        for (int e = lane; e < n; e += 32) {
+        for (int e = lane; e < m; e += 32) {
           double x = wi[e], y = wj[e];
           a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
         }
@@ -60,13 +60,13 @@ __device__ int jacobi_core(int n, double* W, double* V, int ld, int max_sweeps, 
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t);
         double s = c * t;
-        for (int e = lane; e < n; e += 32) {
+        for (int e = lane; e < m; e += 32) {
           double x = wi[e], y = wj[e];
           wi[e] = c * x - s * y;
           wj[e] = s * x + c * y;
         }
-        double* vi = V + (long long)i * ld;
-        double* vj = V + (long long)j * ld;
+        double* vi = V + (long long)i * n;
+        double* vj = V + (long long)j * n;
         for (int e = lane; e < n; e += 32) {
           double x = vi[e], y = vj[e];
           vi[e] = c * x - s * y;
@@ -82,39 +82,42 @@ __device__ int jacobi_core(int n, double* W, double* V, int ld, int max_sweeps, 
   return sweep;
 }
 
-// M, U, V: batch of n x n row-major; S: batch of n.  work: batch * 2 * n * n doubles
-// (only used when n > kSmemN).  *status is set to -1 when a matrix did not converge.
+// M: batch of m x n row-major (m >= n); U: m x n, S: n, V: n x n (row-major),
+// M = U diag(S) V^T with S descending.  work: batch * (m*n + n*n) doubles when
+// the matrix does not fit in shared memory.  *status is set to -1 when a matrix
+// did not converge.
 __global__ void __launch_bounds__(kSvdThreads)
-svd_kernel(int n, const double* __restrict__ M, double* __restrict__ U, double* __restrict__ S,
-           double* __restrict__ V, double* __restrict__ work, int* __restrict__ status,
-           int max_sweeps, double tol) {
+svd_kernel(int m, int n, const double* __restrict__ M, double* __restrict__ U, double* __restrict__ S,
+           double* __restrict__ V, double* __restrict__ work, int* __restrict__ status, int max_sweeps,
+           double tol, int in_smem) {
   extern __shared__ double sm[];
   __shared__ int flag;
-  const long long nn = (long long)n * n;
+  const long long mn = (long long)m * n, nn = (long long)n * n;
   const int b = blockIdx.x;
-  const double* Mb = M + b * nn;
+  const double* Mb = M + b * mn;
   double *W, *Vw;
-  if (n <= kSmemN) { W = sm; Vw = sm + nn; }
-  else { W = work + b * 2 * nn; Vw = W + nn; }
-  // W (column-major) = M;  V = identity
+  if (in_smem) { W = sm; Vw = sm + mn; }
+  else { W = work + b * (mn + nn); Vw = W + mn; }
+  for (long long e = threadIdx.x; e < mn; e += blockDim.x) {
+    int r = (int)(e / n), c = (int)(e % n);
+    W[(long long)c * m + r] = Mb[e];
+  }
   for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
     int r = (int)(e / n), c = (int)(e % n);
-    W[(long long)c * n + r] = Mb[e];
     Vw[(long long)c * n + r] = (r == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  int sw = jacobi_core(n, W, Vw, n, max_sweeps, tol, &flag);
+  int sw = jacobi_core(m, n, W, Vw, max_sweeps, tol, &flag);
   __syncthreads();
-  // singular values = column norms, then order by descending value
   double* Sb = S + (long long)b * n;
   for (int c = threadIdx.x >> 5; c < n; c += blockDim.x >> 5) {
     double a = 0;
-    for (int e = threadIdx.x & 31; e < n; e += 32) a = fma(W[(long long)c * n + e], W[(long long)c * n + e], a);
+    for (int e = threadIdx.x & 31; e < m; e += 32) a = fma(W[(long long)c * m + e], W[(long long)c * m + e], a);
     a = warp_sum(a);
     if ((threadIdx.x & 31) == 0) Sb[c] = sqrt(a);   // unsorted for now
   }
   __syncthreads();
-  double* Ub = U + b * nn;
+  double* Ub = U + b * mn;
   double* Vb = V + b * nn;
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
     double sc = Sb[c];
@@ -123,17 +126,12 @@ svd_kernel(int n, const double* __restrict__ M, double* __restrict__ U, double* 
       double so = Sb[o];
       rank += (so > sc) || (so == sc && o < c);
     }
-    // rank-th column of the outputs
     double inv = sc > 0 ? 1.0 / sc : 0.0;
-    for (int e = 0; e < n; ++e) {
-      Ub[(long long)e * n + rank] = W[(long long)c * n + e] * inv;
-      Vb[(long long)e * n + rank] = Vw[(long long)c * n + e];
-    }
+    for (int e = 0; e < m; ++e) Ub[(long long)e * n + rank] = W[(long long)c * m + e] * inv;
+    for (int e = 0; e < n; ++e) Vb[(long long)e * n + rank] = Vw[(long long)c * n + e];
   }
   __syncthreads();
-  // sort S in place: gather via ranks (second pass; values only)
   if (threadIdx.x == 0 && sw >= max_sweeps) atomicExch(status, -1);   // sticky failure flag
-  __syncthreads();
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
     double sc = Sb[c];
     int rank = 0;
@@ -141,23 +139,26 @@ svd_kernel(int n, const double* __restrict__ M, double* __restrict__ U, double* 
       double so = Sb[o];
       rank += (so > sc) || (so == sc && o < c);
     }
-    // stash sorted value in the workspace column slot of W (no longer needed)
-    W[rank] = sc;
+    W[rank] = sc;   // W is free now; stage the sorted values
   }
   __syncthreads();
   for (int c = threadIdx.x; c < n; c += blockDim.x) Sb[c] = W[c];
 }
 
-void launch_svd(int n, int batch, const double* M, double* U, double* S, double* V,
-                double* work, int* status, cudaStream_t s) {
+static bool fits_smem(int m, int n) { return (long long)(m + n) * n * 8 <= 40 * 1024; }
+
+void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V, double* work,
+                int* status, cudaStream_t s) {
   if (batch == 0 || n == 0) return;
+  SCTM_CHECK(m >= n, "svd expects rows >= columns");
   const int max_sweeps = 60;
-  const double tol = 2.3e-16 * 4.0 * sqrt((double)n);
-  size_t smem = (n <= kSmemN) ? (size_t)2 * n * n * sizeof(double) : 0;
-  svd_kernel<<<batch, kSvdThreads, smem, s>>>(n, M, U, S, V, work, status, max_sweeps, tol);
+  const double tol = 2.3e-16 * 4.0 * sqrt((double)m);
+  const int in_smem = fits_smem(m, n);
+  size_t smem = in_smem ? (size_t)(m + n) * n * sizeof(double) : 0;
+  svd_kernel<<<batch, kSvdThreads, smem, s>>>(m, n, M, U, S, V, work, status, max_sweeps, tol, in_smem);
   SCTM_CUDA(cudaGetLastError());
 }
 
-size_t svd_work_doubles(int n, int batch) { return (n <= kSmemN) ? 0 : (size_t)batch * 2 * n * n; }
+size_t svd_work_doubles(int m, int n, int batch) { return fits_smem(m, n) ? 0 : (size_t)batch * (m + n) * n; }
 
 }  // namespace sctm

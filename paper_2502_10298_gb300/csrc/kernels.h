@@ -7,10 +7,11 @@ namespace sctm {
 template <typename T>
 void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s);
 
-// Batched SVD of n x n row-major matrices: M = U diag(S) V^T, S descending.
-void launch_svd(int n, int batch, const double* M, double* U, double* S, double* V,
+// Batched SVD of m x n row-major matrices (m >= n): M = U diag(S) V^T with
+// U m x n, V n x n, S descending.
+void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V,
                 double* work, int* status, cudaStream_t s);
-size_t svd_work_doubles(int n, int batch);
+size_t svd_work_doubles(int m, int n, int batch);
 
 // out[g] = alpha * in[g] + beta * out[g] over one index group g (strides sa = in, sc = out).
 template <typename T>

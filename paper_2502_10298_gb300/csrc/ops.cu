@@ -239,8 +239,8 @@ Tensor copy(Ctx& c, const Tensor& X) {
 
 // ------------------------------------------------------------------ svd
 SVDResult svd(Ctx& c, const Tensor& M_in, double eps_l) {
-  SCTM_CHECK(M_in.nd == 2 && M_in.shape[0] == M_in.shape[1], "svd expects a square matrix");
-  const int n = M_in.shape[0];
+  SCTM_CHECK(M_in.nd == 2 && M_in.shape[0] >= M_in.shape[1], "svd expects a matrix with rows >= columns");
+  const int m = M_in.shape[0], n = M_in.shape[1];
   bool tap = c.tape.active;
   Tensor M = M_in;
   if (!M.contiguous()) {
@@ -249,19 +249,21 @@ SVDResult svd(Ctx& c, const Tensor& M_in, double eps_l) {
     c.tape.active = tap;
   }
   SVDResult r;
-  r.U = c.empty({n, n});
+  r.U = c.empty({m, n});
   r.S = c.empty({n});
   r.V = c.empty({n, n});
   size_t mk = c.arena.mark();
   double* work = nullptr;
-  size_t wn = svd_work_doubles(n, 1);
+  size_t wn = svd_work_doubles(m, n, 1);
   if (wn) work = c.arena.alloc((long long)wn);
-  launch_svd(n, 1, M.data, r.U.data, r.S.data, r.V.data, work, c.svd_status, c.stream);
-  if (!tap) c.arena.release(mk);  // workspace not needed once the kernel is queued... (stream order)
+  launch_svd(m, n, 1, M.data, r.U.data, r.S.data, r.V.data, work, c.svd_status, c.stream);
+  if (!tap) c.arena.release(mk);  // later work is stream-ordered after the kernel
   if (!tap || !M_in.grad) return r;
   Tensor U = r.U, S = r.S, V = r.V, Min = M_in;
-  c.tape.push([&c, U, S, V, Min, n, eps_l]() {
-    // J = U^T Ubar, K = V^T Vbar
+  // M_bar = U [ F o (J - J^T) S + diag(S_bar) + S F o (K - K^T) ] V^T,
+  // J = U^T U_bar, K = V^T V_bar.  For m > n the projector code uses only S and V
+  // (U_bar = 0), so the (1 - U U^T) U_bar S^-1 V^T term of the thin SVD vanishes.
+  c.tape.push([&c, U, S, V, Min, m, n, eps_l]() {
     bool t = c.tape.active;
     c.tape.active = false;
     Tensor gU = grad_view(U), gV = grad_view(V), gS = grad_view(S);
@@ -269,7 +271,7 @@ SVDResult svd(Ctx& c, const Tensor& M_in, double eps_l) {
     einsum_into(c, "ai,aj->ij", U, gU, J, 1.0, 0.0, false);
     einsum_into(c, "ai,aj->ij", V, gV, K, 1.0, 0.0, false);
     launch_svd_adj_inner(n, S.data, J.data, K.data, gS.data, inner.data, eps_l, c.stream);
-    Tensor T1 = c.empty({n, n});
+    Tensor T1 = c.empty({m, n});
     einsum_into(c, "ai,ij->aj", U, inner, T1, 1.0, 0.0, false);
     einsum_into(c, "aj,bj->ab", T1, V, grad_view(Min), 1.0, 1.0, false);
     c.tape.active = t;

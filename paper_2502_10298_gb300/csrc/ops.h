@@ -35,7 +35,7 @@ Tensor einsum(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, double
 void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, const Tensor& C,
                  double alpha, double beta, bool record);
 
-// Full SVD of a square matrix (2-D, any strides): returns U, S, V with M = U S V^T.
+// SVD of an m x n matrix, m >= n (any strides): M = U S V^T, U m x n, V n x n.
 struct SVDResult {
   Tensor U, S, V;
 };
