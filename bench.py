@@ -1,0 +1,275 @@
+"""Benchmark: energy+gradient evaluations per second of split-CTMRG on GB300.
+
+One step = one call of the engine's ``energy_grad``: initial environment,
+`sweeps` full directional steps (left, top, right, bottom), 2x2-patch energy,
+and the reverse pass through all of it.  Workload (default): 2x2 cell, d=2,
+D=8, chi=128, J1-J2 Heisenberg with J2/J1=0.5, seeded N(0,1) tensors with a
+Neel-biased component (synthetic; ipeps_inputs.config("cfg4")).
+
+Prints one JSON line (rank 0).  Run ``--impl reference`` to time the FP64 CPU
+oracle on the same workload (bounded sample, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ipeps_inputs as I  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe's nominal figure)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload(name, sweeps):
+    A, c = I.config(name)
+    if c["rotated"]:
+        h_nn, h_diag = I.heisenberg_bond_rotated(), None
+    else:
+        h_nn = I.heisenberg_bond()
+        h_diag = c["J2"] * I.heisenberg_bond() if c["J2"] else None
+    if sweeps is None:
+        sweeps = c["bench_sweeps"]
+    desc = (f"{name}: {c['Lx']}x{c['Ly']} cell, d={c['p']}, D={c['D']}, chi={c['chi']}, "
+            f"{'rotated ' if c['rotated'] else ''}Heisenberg J1=1" + (f", J2={c['J2']}" if c["J2"] else "")
+            + f", {sweeps} directional sweeps per evaluation")
+    return A, c, h_nn, h_diag, sweeps, desc
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
+    """Time the FP64 oracle on a bounded sample of the same workload: as many
+    single-column left moves (with every projector) as fit in ~budget_s, then
+    scale to one evaluation = (init +) 4*Ly*sweeps column moves forward, the
+    same again recomputed plus ~2x for the reverse pass (autograd)."""
+    import torch
+    from oracle import ctmrg as C
+    torch.set_num_threads(os.cpu_count() or 1)
+    Ac = C.as_cell(A)
+    t0 = time.perf_counter()
+    env = C.initial_env(Ac, c["chi"])
+    t_init = time.perf_counter() - t0
+    n, t_col = 0, 0.0
+    while t_col < budget_s and n < 8:
+        t1 = time.perf_counter()
+        with torch.no_grad():
+            C.split_column_projectors(Ac, env, n % c["Ly"], c["chi"])
+        t_col += time.perf_counter() - t1
+        n += 1
+    per_col = t_col / n
+    moves = 4 * sweeps
+    cols_per_move = c["Ly"]  # left/right moves; top/bottom use Lx rows (2x2 cell: same)
+    fwd = t_init + moves * cols_per_move * per_col
+    t_eval = fwd * 4.0   # forward + checkpointed recompute + reverse (~2x forward)
+    return {"value": 1.0 / t_eval, "unit": "evals/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n} single-column projector stages of a left move at {name} "
+                      f"({per_col:.2f} s each) + initial environment ({t_init:.2f} s) on the host, "
+                      f"scaled to one energy+gradient evaluation as 4x the forward "
+                      f"({moves} moves x {cols_per_move} columns)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
+    cb = cpu_baseline(args.config, c, A, h_nn, h_diag, sweeps, budget_s=args.cpu_budget)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "evals/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / cb["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+METRIC = "energy+gradient evals/s (split-CTMRG, D=8 chi=128) & TFLOP/s vs peak, vs FP64"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg4")
+    ap.add_argument("--sweeps", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2502_10298_gb300 as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    S.load_library()
+    A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
+    At = torch.tensor(A, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+    s = S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], workspace_bytes=args_ws(c))
+
+    def step():
+        return s.energy_grad(At, sweeps, h_nn, h_diag)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    S.sctm_profile(s.h, True)
+    total_ms = 0.0
+    e_val = None
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        e_val, g = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+    prof = S.sctm_profile(s.h, False)
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    value = world * 1000.0 / ms_per_step
+
+    # end-to-end through the host-buffer C-ABI call (H2D of A, D2H of grad + energy inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.tensor(A).pin_memory().numpy()
+        g_host = torch.empty(A.shape, dtype=torch.float64).pin_memory().numpy()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(1, args.steps)
+        for _ in range(n_e2e):
+            S.energy_grad_host(s.h, A_host, sweeps, h_nn, h_diag, grad_out=g_host)
+        t_e2e = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": world / t_e2e, "unit": "evals/s", "h2d_bytes_per_step": int(A.nbytes),
+               "d2h_bytes_per_step": int(A.nbytes) + 8}
+
+    peaks, src = load_peaks()
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[fam]
+    tot_ms = sum(v["ms"] for v in prof.values())
+    achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else 0.0
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": fam,
+            "share_of_device_time": p["ms"] / tot_ms if tot_ms else None,
+            "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM); no FP64 figure in MEASURED_PEAKS.json",
+            "families": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                             "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else 0.0}
+                         for k, v in prof.items()}}
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(args.config, c, A, h_nn, h_diag, sweeps, budget_s=args.cpu_budget)
+    launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "energy_per_site": e_val, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "cpu_baseline": cpu,
+            "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def args_ws(c):
+    # workspace: checkpoints + one taped sweep; generous on a 280 GB part
+    return int(min(200, max(4, (c["chi"] * c["D"]) ** 2 * c["p"] * 8 * 600 / 2**30)) * 2**30)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

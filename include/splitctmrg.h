@@ -56,7 +56,14 @@ typedef struct {
   int p;                 /* physical dimension                               */
   int D;                 /* bulk bond dimension chi_B                        */
   int chi;               /* environment and interlayer bond dimension        */
-  int precision;         /* 0 = FP64 throughout                              */
+  int precision;         /* 0: FP64 throughout (exact Jacobi SVDs).
+                            1: mixed -- large contractions on the tcgen05 tensor cores
+                               as 3xTF32 (operands split into TF32 hi + lo, FP32
+                               accumulation), small ones in FP32 on the CUDA cores;
+                               projectors from a randomized subspace iteration (2 chi
+                               columns, two power steps) whenever the truncated space
+                               exceeds 2 chi; decompositions in FP64; default cutoff 1e-6.
+                            2: as 1 with every contraction on the CUDA cores (FP32). */
   double svd_cutoff;     /* relative singular-value cutoff of projectors (<=0: 1e-8) */
   double lorentz_eps;    /* Lorentzian broadening of the SVD adjoint (<=0: 1e-36 s_max^4) */
   size_t workspace_bytes;/* device workspace; 0 = library default          */
@@ -112,6 +119,32 @@ SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int swee
 /* Environment of site (x, y) into out_dev, packed in the order C1 T1k T1b C2
  * T2k T2b C3 T3b T3k C4 T4b T4k (chi^2 or chi*D*chi doubles each). */
 SCTM_API int sctm_get_env(sctm_handle h, int x, int y, double* out_dev);
+
+/* Singular value decomposition M = U diag(S) V^T of an m x n row-major
+ * matrix (m >= n) by one-sided Jacobi in FP64 -- the decomposition behind
+ * every projector (Sec. II.B).  U: m x n, S: n (descending), V: n x n, all
+ * device buffers owned by the caller; the handle's workspace is the scratch.
+ * Synchronises; SCTM_ERR_SVD_NOCONV if the sweep limit was reached. */
+SCTM_API int sctm_svd(sctm_handle h, int m, int n, const double* M_dev, double* U_dev, double* S_dev,
+                      double* V_dev);
+
+/* Tensor contraction C = alpha * einsum(spec, A, B) + beta * C on the handle's
+ * stream, in the handle's precision: the primitive under every absorption,
+ * rho network and projector application (Sec. II.B).  spec is an einsum string
+ * such as "ab,bc->ac" (one letter per leg, every letter in at least two of the
+ * three operands); A_dev, B_dev, C_dev are contiguous row-major device
+ * buffers with extents shape_A/B/C (one int per letter).  With beta == 0, C
+ * is not read.  Synchronises. */
+SCTM_API int sctm_einsum(sctm_handle h, const char* spec, const double* A_dev, const int* shape_A,
+                         const double* B_dev, const int* shape_B, double* C_dev, const int* shape_C,
+                         double alpha, double beta);
+
+/* Per-kernel-family timing.  enable=1 starts recording CUDA events around
+ * every kernel launch (on the handle's stream); enable=0 stops and writes
+ * out[3][4] = {contraction, svd, other} x {device ms, launches, algorithmic
+ * flops, algorithmic bytes}.  Not for timed regions of record: the events
+ * themselves serialise nothing but add host overhead. */
+SCTM_API int sctm_profile(sctm_handle h, int enable, double* out);
 
 /* Device workspace high-water mark in bytes. */
 SCTM_API int sctm_workspace_high_water(sctm_handle h, size_t* bytes);

@@ -10,7 +10,7 @@ import torch
 __all__ = [
     "load_library", "Config", "sctm_create", "sctm_destroy", "split_ctmrg_init", "split_ctmrg_move",
     "split_ctmrg_sweeps", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
-    "sctm_get_env", "sctm_workspace_high_water", "SplitCTMRG", "ENV_KEYS", "SctmError",
+    "sctm_get_env", "sctm_workspace_high_water", "sctm_profile", "sctm_svd", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -33,6 +33,7 @@ class Config(ctypes.Structure):
 
 
 _lib = None
+_ip = ctypes.POINTER(ctypes.c_int)
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
@@ -58,6 +59,9 @@ def load_library(path: str = LIB_PATH):
         "energy_grad_host": (i, [vp, _dp, i, _dp, _dp, _dp, _dp]),
         "sctm_get_env": (i, [vp, i, i, vp]),
         "sctm_workspace_high_water": (i, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+        "sctm_profile": (i, [vp, i, _dp]),
+        "sctm_svd": (i, [vp, i, i, vp, vp, vp, vp]),
+        "sctm_einsum": (i, [vp, ctypes.c_char_p, vp, _ip, vp, _ip, vp, _ip, d, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -161,6 +165,50 @@ def sctm_get_env(h, x, y, chi, D):
         out[k] = buf[off:off + n].view(shape)
         off += n
     return out
+
+
+PROFILE_FAMILIES = ("contract", "svd", "other")
+
+
+def sctm_profile(h, enable: bool):
+    """enable=True starts per-family event timing; enable=False returns
+    {family: dict(ms, launches, flops, bytes)} and stops it."""
+    out = np.zeros(12)
+    _check(h, _lib.sctm_profile(h, 1 if enable else 0, out.ctypes.data_as(_dp)))
+    if enable:
+        return None
+    return {f: dict(ms=out[4 * i], launches=int(out[4 * i + 1]), flops=out[4 * i + 2], bytes=out[4 * i + 3])
+            for i, f in enumerate(PROFILE_FAMILIES)}
+
+
+def sctm_svd(h, M: torch.Tensor):
+    """(U, S, V) of a CUDA float64 matrix with rows >= columns (one-sided Jacobi)."""
+    m, n = M.shape
+    M = M.contiguous()
+    U = torch.empty((m, n), dtype=torch.float64, device=M.device)
+    S = torch.empty((n,), dtype=torch.float64, device=M.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=M.device)
+    _check(h, _lib.sctm_svd(h, m, n, _dev(M), _dev(U), _dev(S), _dev(V)))
+    return U, S, V
+
+
+def sctm_einsum(h, spec: str, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None, alpha=1.0, beta=0.0,
+                out_shape=None):
+    """C = alpha * einsum(spec, A, B) + beta * C on CUDA float64 tensors, in the
+    handle's precision (3xTF32 tensor cores for large contractions when mixed)."""
+    A, B = A.contiguous(), B.contiguous()
+    if C is None:
+        ins, out = spec.split("->")
+        la, lb = ins.split(",")
+        size = dict(zip(la, A.shape))
+        size.update(zip(lb, B.shape))
+        C = torch.empty([size[ch] for ch in out], dtype=torch.float64, device=A.device)
+    assert C.is_contiguous()
+    def shp(t):
+        return (ctypes.c_int * t.dim())(*t.shape)
+    sa, sb, sc = shp(A), shp(B), shp(C)
+    _check(h, _lib.sctm_einsum(h, spec.encode(), _dev(A), sa, _dev(B), sb, _dev(C), sc, float(alpha), float(beta)))
+    return C
 
 
 def sctm_workspace_high_water(h) -> int:

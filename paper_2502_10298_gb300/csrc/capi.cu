@@ -6,6 +6,7 @@
 
 #include "../../include/splitctmrg.h"
 #include "ctmrg.h"
+#include "prof.h"
 
 using namespace sctm;
 
@@ -166,11 +167,16 @@ void read_env_grad(sctm_handle h, double* g) {
 }
 
 void check_svd(sctm_handle h) {
-  // the SVD kernels record -1 in the status word when they ran out of sweeps
-  int st = 0;
-  SCTM_CUDA(cudaMemcpyAsync(&st, h->c.svd_status, sizeof(int), cudaMemcpyDeviceToHost, h->c.stream));
+  // the SVD kernels record -1 in status word 0 when they ran out of sweeps; the
+  // tensor-core contraction records -2 in word 32 when a pipeline wait timed out
+  int st[33] = {0};
+  SCTM_CUDA(cudaMemcpyAsync(st, h->c.svd_status, sizeof(st), cudaMemcpyDeviceToHost, h->c.stream));
   SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
-  if (st < 0) {
+  if (st[32] < 0) {
+    SCTM_CUDA(cudaMemsetAsync(h->c.svd_status + 32, 0, sizeof(int), h->c.stream));
+    throw CudaError("tensor-core contraction: pipeline wait timed out");
+  }
+  if (st[0] < 0) {
     SCTM_CUDA(cudaMemsetAsync(h->c.svd_status, 0, sizeof(int), h->c.stream));
     throw std::runtime_error("svd: no convergence");
   }
@@ -186,42 +192,47 @@ void sweep_untaped(sctm_handle h) {
   }
 }
 
+// Energy per site, one 2x2 patch at a time; with `seed` the reverse pass of
+// every patch runs right after it (adjoints accumulate in the leaves' gradient
+// buffers), so only one patch's intermediates are ever held.
 double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed) {
-  std::vector<EnergyTerm> terms = energy_terms(h->c, h->P, h->cell, hn, hd);
-  std::vector<double> nums(terms.size()), dens(terms.size());
-  for (size_t i = 0; i < terms.size(); ++i) {
-    SCTM_CUDA(cudaMemcpyAsync(&nums[i], terms[i].num.data, sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
-    SCTM_CUDA(cudaMemcpyAsync(&dens[i], terms[i].den.data, sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
-  }
-  SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  Ctx& c = h->c;
+  EnergyOps ops = energy_ops(c, h->P, hn, hd);
   double E = 0;
-  for (size_t i = 0; i < terms.size(); ++i) E += terms[i].w * nums[i] / dens[i];
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y) {
+      size_t mk = c.arena.mark();
+      std::vector<EnergyTerm> terms = energy_patch(c, h->P, h->cell, ops, x, y);
+      std::vector<double> nums(terms.size()), dens(terms.size());
+      for (size_t i = 0; i < terms.size(); ++i) {
+        SCTM_CUDA(cudaMemcpyAsync(&nums[i], terms[i].num.data, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        SCTM_CUDA(cudaMemcpyAsync(&dens[i], terms[i].den.data, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      }
+      SCTM_CUDA(cudaStreamSynchronize(c.stream));
+      for (size_t i = 0; i < terms.size(); ++i) E += terms[i].w * nums[i] / dens[i];
+      if (seed) {
+        // dE/dnum = w/den ; dE/dden = -w num/den^2 (accumulated per shared den)
+        std::vector<std::pair<double*, double>> acc;
+        auto add = [&](double* p, double v) {
+          for (auto& a : acc)
+            if (a.first == p) { a.second += v; return; }
+          acc.push_back({p, v});
+        };
+        for (size_t i = 0; i < terms.size(); ++i) {
+          SCTM_CHECK(terms[i].num.grad && terms[i].den.grad, "energy terms without gradient buffers");
+          add(terms[i].num.grad, terms[i].w / dens[i]);
+          add(terms[i].den.grad, -terms[i].w * nums[i] / (dens[i] * dens[i]));
+        }
+        std::vector<double> hostv(acc.size());
+        for (size_t i = 0; i < acc.size(); ++i) hostv[i] = acc[i].second;
+        for (size_t i = 0; i < acc.size(); ++i)
+          SCTM_CUDA(cudaMemcpyAsync(acc[i].first, &hostv[i], sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        c.tape.backward();
+        SCTM_CUDA(cudaStreamSynchronize(c.stream));   // hostv must outlive the copies
+      }
+      c.arena.release(mk);
+    }
   if (!std::isfinite(E)) throw std::runtime_error("non-finite energy");
-  if (seed) {
-    // dE/dnum = w/den ; dE/dden = -w num/den^2 (accumulated per shared den)
-    std::vector<std::pair<double*, double>> gs;
-    std::vector<double> hostv;
-    for (size_t i = 0; i < terms.size(); ++i) {
-      double gn = terms[i].w / dens[i];
-      double gd = -terms[i].w * nums[i] / (dens[i] * dens[i]);
-      SCTM_CHECK(terms[i].num.grad && terms[i].den.grad, "energy terms without gradient buffers");
-      gs.push_back({terms[i].num.grad, gn});
-      gs.push_back({terms[i].den.grad, gd});
-    }
-    // accumulate on host per distinct pointer, then upload
-    std::vector<std::pair<double*, double>> acc;
-    for (auto& g : gs) {
-      bool found = false;
-      for (auto& a : acc)
-        if (a.first == g.first) a.second += g.second, found = true;
-      if (!found) acc.push_back(g);
-    }
-    hostv.resize(acc.size());
-    for (size_t i = 0; i < acc.size(); ++i) hostv[i] = acc[i].second;
-    for (size_t i = 0; i < acc.size(); ++i)
-      SCTM_CUDA(cudaMemcpyAsync(acc[i].first, &hostv[i], sizeof(double), cudaMemcpyHostToDevice, h->c.stream));
-    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
-  }
   return E;
 }
 
@@ -235,9 +246,13 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
   int rc = guard(h.get(), [&]() {
     SCTM_CHECK(cfg->Lx >= 1 && cfg->Ly >= 1 && cfg->p >= 1 && cfg->D >= 1 && cfg->chi >= 1, "bad dimensions");
     SCTM_CHECK(cfg->D * cfg->D <= cfg->chi, "chi must be >= D^2");
-    SCTM_CHECK(cfg->precision == 0, "only precision 0 (FP64) is available");
+    SCTM_CHECK(cfg->precision >= 0 && cfg->precision <= 2, "precision must be 0 (FP64), 1 or 2 (mixed)");
     Params& P = h->P;
     P.Lx = cfg->Lx, P.Ly = cfg->Ly, P.p = cfg->p, P.D = cfg->D, P.chi = cfg->chi;
+    P.mixed = (cfg->precision >= 1);
+    h->c.fp32_compute = P.mixed;
+    h->c.tensor_cores = (cfg->precision == 1);
+    if (P.mixed) P.cutoff = 1e-6;   // FP32 contractions: singular values below ~1e-7 s_max are rounding noise
     if (cfg->svd_cutoff > 0) P.cutoff = cfg->svd_cutoff;
     if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
     h->c.stream = (cudaStream_t)stream;
@@ -401,7 +416,6 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
     c.tape.active = true;
     bind_leaves(h, ck + sweeps * nE);
     *e_per_site = energy_value(h, h_nn_host, h_diag_host, true);
-    c.tape.backward();
     read_env_grad(h, gbuf);
     c.tape.active = false;
     c.arena.release(top);
@@ -463,6 +477,64 @@ int sctm_get_env(sctm_handle h, int x, int y, double* out_dev) {
     SCTM_CUDA(cudaMemcpyAsync(out_dev, h->store + site_index(h, x, y) * h->env_site, h->env_site * sizeof(double),
                               cudaMemcpyDeviceToDevice, h->c.stream));
     SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  });
+}
+
+int sctm_svd(sctm_handle h, int m, int n, const double* M_dev, double* U_dev, double* S_dev, double* V_dev) {
+  return guard(h, [&]() {
+    SCTM_CHECK(m >= n && n >= 1 && M_dev && U_dev && S_dev && V_dev, "bad svd arguments");
+    size_t mk = h->c.arena.mark();
+    double* work = nullptr;
+    size_t wn = svd_work_doubles(m, n, 1);
+    if (wn) work = h->c.arena.alloc((long long)wn);
+    launch_svd(m, n, 1, M_dev, U_dev, S_dev, V_dev, work, h->c.svd_status, h->c.stream);
+    check_svd(h);
+    h->c.arena.release(mk);
+  });
+}
+
+int sctm_einsum(sctm_handle h, const char* spec, const double* A_dev, const int* shape_A, const double* B_dev,
+                const int* shape_B, double* C_dev, const int* shape_C, double alpha, double beta) {
+  return guard(h, [&]() {
+    SCTM_CHECK(spec && A_dev && B_dev && C_dev && shape_A && shape_B && shape_C, "null argument");
+    std::string s(spec);
+    size_t comma = s.find(','), arrow = s.find("->");
+    SCTM_CHECK(comma != std::string::npos && arrow != std::string::npos && comma < arrow, "bad einsum spec");
+    const int nd[3] = {(int)comma, (int)(arrow - comma - 1), (int)(s.size() - arrow - 2)};
+    const int* shp[3] = {shape_A, shape_B, shape_C};
+    double* ptr[3] = {const_cast<double*>(A_dev), const_cast<double*>(B_dev), C_dev};
+    Tensor t[3];
+    for (int i = 0; i < 3; ++i) {
+      SCTM_CHECK(nd[i] >= 1 && nd[i] <= kMaxDims, "einsum rank out of range");
+      t[i].data = ptr[i];
+      t[i].nd = nd[i];
+      long long st = 1;
+      for (int j = nd[i] - 1; j >= 0; --j) {
+        SCTM_CHECK(shp[i][j] >= 1, "einsum extent must be >= 1");
+        t[i].shape[j] = shp[i][j];
+        t[i].stride[j] = st;
+        st *= shp[i][j];
+      }
+    }
+    bool tp = h->c.tape.active;
+    h->c.tape.active = false;
+    einsum_into(h->c, spec, t[0], t[1], t[2], alpha, beta, false);
+    h->c.tape.active = tp;
+    check_svd(h);
+  });
+}
+
+int sctm_profile(sctm_handle h, int enable, double* out) {
+  return guard(h, [&]() {
+    if (enable) {
+      SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+      prof_enable(true);
+    } else {
+      SCTM_CHECK(out, "null output");
+      SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+      prof_collect(out);
+      prof_enable(false);
+    }
   });
 }
 

@@ -1,4 +1,4 @@
-// Strided batched tensor contraction on CUDA cores (FP64 / FP32 storage).
+// Strided batched tensor contraction on CUDA cores (FP64 storage; FP64 or FP32 arithmetic).
 //
 // Every pairwise contraction of the split-CTMRG networks (absorption
 // equations, rho networks, M = rho^B rho^T, projector application) is
@@ -8,23 +8,26 @@
 // operand elements through per-tile offset tables kept in shared memory.
 #include "common.h"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sctm {
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
+template <typename T, typename Tc, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   __shared__ long long offAm[BM], offCm[BM], offBn[BN], offCn[BN];
   __shared__ long long offAk[BK], offBk[BK];
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  __shared__ Tc As[BK][BM + 1];
+  __shared__ Tc Bs[BK][BN + 1];
 
   const int tid = threadIdx.x;
   const long long b = blockIdx.z;
-  const long long m0 = (long long)blockIdx.y * BM;
-  const long long n0 = (long long)blockIdx.x * BN;
+  const long long ntn = (d.N + BN - 1) / BN;
+  const long long tile = blockIdx.x;
+  const long long m0 = (tile / ntn) * BM;
+  const long long n0 = (tile % ntn) * BN;
   const long long boA = group_offset(d.bat, d.bat.sa, b);
   const long long boB = group_offset(d.bat, d.bat.sb, b);
   const long long boC = group_offset(d.bat, d.bat.sc, b);
@@ -49,11 +52,11 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
     }
   }
   const int ty = tid / TX, tx = tid % TX;
-  T acc[TM][TN];
+  Tc acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = Tc(0);
 
   for (long long k0 = 0; k0 < d.K; k0 += BK) {
     __syncthreads();
@@ -68,19 +71,19 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
       if (d.a_k_inner) { kk = idx % BK; mm = idx / BK; }
       else { mm = idx % BM; kk = idx / BM; }
       long long om = offAm[mm], ok = offAk[kk];
-      As[kk][mm] = (om >= 0 && ok >= 0) ? A[om + ok] : T(0);
+      As[kk][mm] = (om >= 0 && ok >= 0) ? (Tc)A[om + ok] : Tc(0);
     }
     for (int idx = tid; idx < BN * BK; idx += NT) {
       int nn, kk;
       if (d.b_n_inner) { nn = idx % BN; kk = idx / BN; }
       else { kk = idx % BK; nn = idx / BK; }
       long long on = offBn[nn], ok = offBk[kk];
-      Bs[kk][nn] = (on >= 0 && ok >= 0) ? B[on + ok] : T(0);
+      Bs[kk][nn] = (on >= 0 && ok >= 0) ? (Tc)B[on + ok] : Tc(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[TM], bb[TN];
+      Tc a[TM], bb[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
 #pragma unroll
@@ -103,7 +106,7 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
       int nn = tx + j * TX;
       long long on = offCn[nn];
       if (on < 0) continue;
-      T v = alpha * acc[i][j];
+      T v = alpha * (T)acc[i][j];
       if (d.beta != 0.0) v += beta * C[om + on];
       C[om + on] = v;
     }
@@ -111,16 +114,22 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
 }
 
 template <typename T>
-void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s) {
+void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute) {
   if (d.M == 0 || d.N == 0 || d.B == 0) return;
   constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
-  dim3 grid((unsigned)((d.N + BN - 1) / BN), (unsigned)((d.M + BM - 1) / BM), (unsigned)d.B);
-  SCTM_CHECK(grid.y <= 65535 && grid.z <= 65535, "contraction too large for grid");
-  contract_kernel<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C);
+  long long tiles = ((d.N + BN - 1) / BN) * ((d.M + BM - 1) / BM);
+  SCTM_CHECK(tiles < (1LL << 31) && d.B <= 65535, "contraction too large for grid");
+  dim3 grid((unsigned)tiles, 1, (unsigned)d.B);
+  // algorithmic work: 2 B M N K flops; bytes = operands read once + result written
+  ProfScope ps(PF_CONTRACT, s, 2.0 * d.B * d.M * d.N * d.K,
+               (double)sizeof(T) * d.B * (d.M * d.K + d.K * d.N + d.M * d.N * (d.beta != 0 ? 2 : 1)));
+  if (fp32_compute)
+    contract_kernel<T, float, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C);
+  else
+    contract_kernel<T, T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C);
   SCTM_CUDA(cudaGetLastError());
 }
 
-template void launch_contract<double>(const ContractDesc&, const double*, const double*, double*, cudaStream_t);
-template void launch_contract<float>(const ContractDesc&, const float*, const float*, float*, cudaStream_t);
+template void launch_contract<double>(const ContractDesc&, const double*, const double*, double*, cudaStream_t, bool);
 
 }  // namespace sctm

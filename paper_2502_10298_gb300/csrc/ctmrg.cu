@@ -5,6 +5,7 @@
 // Projectors: Sec. II.B (Fig. 3) and App. A (Figs. 7-9).  The other three
 // moves are left moves in a transposed or 180-degree rotated frame; frames are
 // pure stride/handle permutations, so they cost nothing on the device.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -14,6 +15,176 @@
 namespace sctm {
 
 // ------------------------------------------------------------------ projector
+static Tensor no_grad(Tensor t) {
+  t.grad = nullptr;
+  return t;
+}
+
+// Orthonormal basis of the columns of Y (n x r): eigen-decompose G = Y^T Y
+// (FP64 Jacobi) and return Y W Lambda^-1/2, dropping eigenvalues below
+// 1e-14 lambda_max (numerically dependent directions).  Not taped.
+static Tensor orthonormal_columns(Ctx& c, const Tensor& Y) {
+  const int r = Y.shape[1];
+  Tensor G = einsum(c, "ai,aj->ij", Y, Y);
+  SVDResult e = svd(c, G, 0.0);
+  Tensor w = spectrum_map(c, e.S, r, 1e-14, 0);   // lambda^-1/2
+  Tensor W = scale_dim(c, e.V, 1, w);
+  return einsum(c, "ai,ij->aj", Y, W);
+}
+
+// Batched SVD of equally shaped square matrices (untaped): one kernel launch.
+static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
+  const int nb = (int)Ms.size();
+  std::vector<SVDResult> out(nb);
+  if (nb == 0) return out;
+  const int n = Ms[0].shape[0];
+  Tensor Mb = c.empty({nb, n, n}), Ub = c.empty({nb, n, n}), Sb = c.empty({nb, n}), Vb = c.empty({nb, n, n});
+  for (int i = 0; i < nb; ++i) copy_into(c, Ms[i], Mb.sub(0, i));
+  size_t wn = svd_work_doubles(n, n, nb);
+  double* work = wn ? c.arena.alloc((long long)wn) : nullptr;
+  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream);
+  for (int i = 0; i < nb; ++i) out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};
+  return out;
+}
+
+// Orthonormal bases of many n_i x r blocks at once (see orthonormal_columns).
+static std::vector<Tensor> orthonormal_columns_batch(Ctx& c, const std::vector<Tensor>& Ys) {
+  std::vector<Tensor> Gs, out;
+  for (auto& Y : Ys) Gs.push_back(einsum(c, "ai,aj->ij", Y, Y));
+  std::vector<SVDResult> e = svd_batch(c, Gs);
+  for (size_t i = 0; i < Ys.size(); ++i) {
+    const int r = Ys[i].shape[1];
+    Tensor w = spectrum_map(c, e[i].S, r, 1e-14, 0);
+    out.push_back(einsum(c, "ai,ij->aj", Ys[i], scale_dim(c, e[i].V, 1, w)));
+  }
+  return out;
+}
+
+// Top-r singular triplets of M = rhoB rhoT (beta x beta, never formed) by
+// randomized subspace iteration with two power steps (Halko, Martinsson,
+// Tropp 2011, Alg. 4.4), in FP64 arithmetic for the small decompositions.
+// Returns U (beta x r), S (r), V (beta x r) with M ~ U S V^T.  Not taped.
+struct Trunc {
+  Tensor U, S, V;
+};
+static Trunc randomized_svd(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, int r) {
+  const int b = rhoT.shape[1];
+  Tensor Om = c.empty({b, r});
+  launch_gaussian(b, r, 0x5eedULL + (unsigned long long)b * 131 + r, Om.data, c.stream);
+  Tensor Y = einsum(c, "ab,bj->aj", rhoB, einsum(c, "ab,bj->aj", rhoT, Om));        // M Omega
+  for (int q = 0; q < 2; ++q) {
+    Tensor Q = orthonormal_columns(c, Y);
+    Tensor Z = einsum(c, "ba,bj->aj", rhoT, einsum(c, "ba,bj->aj", rhoB, Q));     // M^T Q
+    Y = einsum(c, "ab,bj->aj", rhoB, einsum(c, "ab,bj->aj", rhoT, Z));            // M M^T Q
+  }
+  Tensor Q = orthonormal_columns(c, Y);                                          // beta x r
+  Tensor Bt = einsum(c, "ba,bj->aj", rhoT, einsum(c, "ba,bj->aj", rhoB, Q));     // M^T Q = B^T
+  Tensor G = einsum(c, "ai,aj->ij", Bt, Bt);                                     // B B^T
+  SVDResult e = svd(c, G, 0.0);                                                  // = W Lambda W^T
+  Trunc t;
+  t.S = spectrum_map(c, e.S, r, 0.0, 1);                                         // sqrt(lambda)
+  // lambda^-1/2; eigenvalues of the FP64 Gram matrix below 1e-14 lambda_max are
+  // rounding noise (singular values below 1e-7 s_max, under every cutoff used)
+  Tensor sinv = spectrum_map(c, e.S, r, 1e-14, 0);
+  t.U = einsum(c, "ai,ij->aj", Q, e.V);                                          // Q W
+  t.V = scale_dim(c, einsum(c, "ai,ij->aj", Bt, e.V), 1, sinv);                  // B^T W S^-1
+  return t;
+}
+
+static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB,
+                                               int r) {
+  const size_t nb = rT.size();
+  std::vector<Tensor> Y(nb);
+  for (size_t i = 0; i < nb; ++i) {
+    const int b = rT[i].shape[1];
+    Tensor Om = c.empty({b, r});
+    launch_gaussian(b, r, 0x5eedULL + (unsigned long long)b * 131 + r, Om.data, c.stream);
+    Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Om));       // M Omega
+  }
+  std::vector<Tensor> Q = orthonormal_columns_batch(c, Y);
+  for (int q = 0; q < 2; ++q) {   // two power steps
+    for (size_t i = 0; i < nb; ++i) {
+      Tensor Z = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));  // M^T Q
+      Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Z));        // M M^T Q
+    }
+    Q = orthonormal_columns_batch(c, Y);
+  }
+  std::vector<Tensor> Bt(nb), G(nb);
+  for (size_t i = 0; i < nb; ++i) {
+    Bt[i] = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));    // B^T = M^T Q
+    G[i] = einsum(c, "ai,aj->ij", Bt[i], Bt[i]);
+  }
+  std::vector<SVDResult> e = svd_batch(c, G);
+  std::vector<Trunc> out(nb);
+  for (size_t i = 0; i < nb; ++i) {
+    out[i].S = spectrum_map(c, e[i].S, r, 0.0, 1);
+    Tensor sinv = spectrum_map(c, e[i].S, r, 1e-14, 0);   // see randomized_svd
+    out[i].U = einsum(c, "ai,ij->aj", Q[i], e[i].V);
+    out[i].V = scale_dim(c, einsum(c, "ai,ij->aj", Bt[i], e[i].V), 1, sinv);
+  }
+  return out;
+}
+
+// Reverse pass of a truncated SVD (U_r, S_r, V_r) of M = rhoB rhoT, treating
+// the singular values beyond r as zero (the projector uses the first k < r
+// triplets, so the coupling to the r - k next ones is exact):
+//   M_bar = U X V^T + (U_bar - U J) S^-1 V^T + U S^-1 (V_bar - V K)^T,
+//   X = F o (J - J^T) S + diag(S_bar) + S F o (K - K^T), J = U^T U_bar, K = V^T V_bar,
+// applied without forming M_bar:  rhoB_bar += M_bar rhoT^T, rhoT_bar += rhoB^T M_bar.
+static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
+                                  const Tensor& V, double eps_l) {
+  const int k = S.shape[0];
+  Tensor gU = no_grad(U), gV = no_grad(V), gS = no_grad(S);
+  gU.data = U.grad;
+  gV.data = V.grad;
+  gS.data = S.grad;
+  Tensor J = c.empty({k, k}), K = c.empty({k, k}), X = c.empty({k, k});
+  einsum_into(c, "ai,aj->ij", U, gU, J, 1.0, 0.0, false);
+  einsum_into(c, "ai,aj->ij", V, gV, K, 1.0, 0.0, false);
+  launch_svd_adj_inner(k, S.data, J.data, K.data, gS.data, X.data, eps_l, c.stream);
+  // 1/s on kept entries, applied as two scalings by s^-1/2
+  Tensor r = c.empty({k});
+  launch_spectrum_map(1, k, k, S.data, r.data, 1e-14, 0, c.stream);
+  Tensor A = c.empty({(int)U.shape[0], k}), Bm = c.empty({(int)V.shape[0], k});
+  // A = (U_bar - U J) S^-1 ; B = (V_bar - V K) S^-1
+  einsum_into(c, "ai,ij->aj", U, J, A, -1.0, 0.0, false);
+  launch_copy<double>([&]() { Group g; g.nd = 2; g.size[0] = U.shape[0]; g.size[1] = k;
+                              g.sa[0] = k; g.sa[1] = 1; g.sc[0] = k; g.sc[1] = 1; return g; }(),
+                      1.0, gU.data, 1.0, A.data, c.stream);
+  einsum_into(c, "ai,ij->aj", V, K, Bm, -1.0, 0.0, false);
+  launch_copy<double>([&]() { Group g; g.nd = 2; g.size[0] = V.shape[0]; g.size[1] = k;
+                              g.sa[0] = k; g.sa[1] = 1; g.sc[0] = k; g.sc[1] = 1; return g; }(),
+                      1.0, gV.data, 1.0, Bm.data, c.stream);
+  launch_scale_rc(1, U.shape[0], k, A.data, r.data, 0, false, c.stream);
+  launch_scale_rc(1, U.shape[0], k, A.data, r.data, 0, false, c.stream);
+  launch_scale_rc(1, V.shape[0], k, Bm.data, r.data, 0, false, c.stream);
+  launch_scale_rc(1, V.shape[0], k, Bm.data, r.data, 0, false, c.stream);
+  // L1 = U X + A
+  Tensor L1 = c.empty({(int)U.shape[0], k});
+  einsum_into(c, "ai,ij->aj", U, X, L1, 1.0, 0.0, false);
+  launch_axpy(L1.numel(), 1.0, A.data, L1.data, c.stream);
+  // rhoB_bar += L1 (V^T rhoT^T) + U (B^T rhoT^T)
+  if (rhoB.grad) {
+    Tensor gB = no_grad(rhoB);
+    gB.data = rhoB.grad;
+    Tensor VR = c.empty({k, (int)rhoT.shape[0]}), BR = c.empty({k, (int)rhoT.shape[0]});
+    einsum_into(c, "bj,ab->ja", V, rhoT, VR, 1.0, 0.0, false);
+    einsum_into(c, "bj,ab->ja", Bm, rhoT, BR, 1.0, 0.0, false);
+    einsum_into(c, "bj,ja->ba", L1, VR, gB, 1.0, 1.0, false);
+    einsum_into(c, "bj,ja->ba", U, BR, gB, 1.0, 1.0, false);
+  }
+  // rhoT_bar += (rhoB^T L1) V^T + (rhoB^T U) B^T
+  if (rhoT.grad) {
+    Tensor gT = no_grad(rhoT);
+    gT.data = rhoT.grad;
+    Tensor RL = c.empty({(int)rhoB.shape[1], k}), RU = c.empty({(int)rhoB.shape[1], k});
+    einsum_into(c, "ba,bj->aj", rhoB, L1, RL, 1.0, 0.0, false);
+    einsum_into(c, "ba,bj->aj", rhoB, U, RU, 1.0, 0.0, false);
+    einsum_into(c, "aj,bj->ab", RL, V, gT, 1.0, 1.0, false);
+    einsum_into(c, "aj,bj->ab", RU, Bm, gT, 1.0, 1.0, false);
+  }
+}
+
 // rhoT: alpha x beta (upper half), rhoB: beta x alpha (lower half).
 // M = rhoB rhoT has rank <= alpha; when alpha < beta both halves are reduced
 // first (App. A: decompose rho^T and rho^B before multiplying them), here by
@@ -22,16 +193,85 @@ namespace sctm {
 //   rhoB   = Q_B S_B V_B^T -> rhoB = Q_B L_B^T with L_B = V_B S_B,
 //   K = L_B^T L_T = U S V^T,  P_up = S^-1/2 U^T L_B^T,  P_dn = L_T V S^-1/2,
 // which equals S^-1/2 U~^T rhoB and rhoT V~ S^-1/2 for the full M.
+// Mixed mode with alpha > 2 chi: the chi leading triplets of M come from a
+// randomized subspace iteration (randomized_svd) and the reverse pass uses
+// the truncated-SVD adjoint above.
+static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, const Trunc& t) {
+  const int k = P.chi;
+  bool tap = c.tape.active;
+  {
+    // leaves U_r, S_r, V_r with gradient buffers when taping; the projector
+    // uses the first k triplets, the reverse pass couples them to all r
+    Tensor Ur = copy(c, t.U), Vr = copy(c, t.V), Sr = copy(c, t.S);
+    Tensor Uk = Ur, Vk = Vr, Sk = Sr;
+    Uk.shape[1] = k;
+    Vk.shape[1] = k;
+    Sk.shape[0] = k;
+    if (tap) {
+      Tensor rT = rhoT, rB = rhoB, U = Ur, S = Sr, V = Vr;
+      double eps = P.eps_l;
+      c.tape.push([&c, rT, rB, U, S, V, eps]() {
+        bool t2 = c.tape.active;
+        c.tape.active = false;
+        truncated_svd_adjoint(c, rT, rB, U, S, V, eps);
+        c.tape.active = t2;
+      });
+    }
+    Tensor w = spectrum_map(c, Sk, k, P.cutoff, 0);
+    Tensor up = scale_dim(c, einsum(c, "ik,ia->ka", Uk, rhoB), 0, w);
+    Tensor dn = scale_dim(c, einsum(c, "ai,ik->ak", rhoT, Vk), 1, w);
+    Tensor sg = row_signs(c, up);
+    up = scale_dim(c, up, 0, sg);
+    dn = scale_dim(c, dn, 1, sg);
+    return ProjPair{up, dn, Sk};
+  }
+}
+
+static bool use_randomized(const Params& P, const Tensor& rhoT) {
+  return P.mixed && std::min(rhoT.shape[0], rhoT.shape[1]) > 2 * P.chi;
+}
+
+std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB) {
+  std::vector<ProjPair> out(rT.size());
+  std::vector<int> ri;
+  std::vector<Tensor> bT, bB;
+  for (size_t i = 0; i < rT.size(); ++i) {
+    if (use_randomized(P, rT[i])) {
+      ri.push_back((int)i);
+      bT.push_back(rT[i]);
+      bB.push_back(rB[i]);
+    } else {
+      out[i] = projector(c, P, rT[i], rB[i]);
+    }
+  }
+  if (!ri.empty()) {
+    bool tap = c.tape.active;
+    c.tape.active = false;
+    std::vector<Trunc> t = randomized_svd_batch(c, bT, bB, 2 * P.chi);
+    c.tape.active = tap;
+    for (size_t j = 0; j < ri.size(); ++j) out[ri[j]] = finish_randomized(c, P, bT[j], bB[j], t[j]);
+  }
+  return out;
+}
+
 ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB) {
   const int a = rhoT.shape[0], b = rhoT.shape[1];
   SCTM_CHECK(rhoB.shape[0] == b && rhoB.shape[1] == a, "projector: rho shapes do not match");
+  const int k = P.chi;
+  if (use_randomized(P, rhoT)) {
+    bool tap = c.tape.active;
+    c.tape.active = false;
+    Trunc t = randomized_svd(c, rhoT, rhoB, 2 * k);
+    c.tape.active = tap;
+    return finish_randomized(c, P, rhoT, rhoB, t);
+  }
   Tensor left, right;  // core = left @ right  (n x n), P_up = w U^T left, P_dn = right V w
   if (a < b) {
     SVDResult eT = svd(c, rhoT.rev(), P.eps_l);   // rhoT^T: b x a
     SVDResult eB = svd(c, rhoB, P.eps_l);         // b x a
     Tensor LT = scale_dim(c, eT.V, 1, eT.S);      // a x a
     Tensor LB = scale_dim(c, eB.V, 1, eB.S);
-    left = LB.rev();                         // L_B^T
+    left = LB.rev();                              // L_B^T
     right = LT;
   } else {
     left = rhoB;
@@ -39,7 +279,6 @@ ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rh
   }
   Tensor M = einsum(c, "ik,kj->ij", left, right);
   const int n = M.shape[0];
-  const int k = P.chi;
   SCTM_CHECK(k <= n, "projector: chi larger than the decomposed space");
   SVDResult r = svd(c, M, P.eps_l);
   Tensor w = spectrum_map(c, r.S, k, P.cutoff, 0);
@@ -262,25 +501,40 @@ void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& o
   const int Lx = cell.Lx;
   const int D = P.D, p = P.p, chi = P.chi;
   out.g.resize(Lx); out.y.resize(Lx); out.t.resize(Lx); out.r.resize(Lx); out.K.resize(Lx);
-  for (int x = 0; x < Lx; ++x)
-    out.g[x] = shaped(projector(c, P, green_rhoT(c, cell.e(x, y), cell.a(x, y)),
-                                green_rhoB(c, cell.e(x + 1, y), cell.a(x + 1, y))), chi, D);
-  for (int x = 0; x < Lx; ++x)
-    out.y[x] = shaped(projector(c, P, yellow_rhoT(c, cell.e(x, y), cell.a(x, y)),
-                                yellow_rhoB(c, cell.e(x, y), cell.a(x, y))), chi, D);
-  for (int x = 0; x < Lx; ++x)
-    out.K[x] = ket_stage(c, cell.e(x, y), cell.a(x, y), out.g[(x + Lx - 1) % Lx], out.y[x], out.g[x]);
+  // ket stage: green (rows x | x+1) and yellow (row x) of every row, batched
+  std::vector<Tensor> rT, rB;
   for (int x = 0; x < Lx; ++x) {
-    int xp = (x + 1) % Lx;
-    out.t[x] = shaped(projector(c, P, teal_rhoT(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1),
-                                                cell.a(x, y + 1)),
-                                teal_rhoB(c, cell.e(xp, y), cell.a(xp, y), out.K[xp], cell.e(xp, y + 1),
-                                          cell.a(xp, y + 1))), chi, D);
+    rT.push_back(green_rhoT(c, cell.e(x, y), cell.a(x, y)));
+    rB.push_back(green_rhoB(c, cell.e(x + 1, y), cell.a(x + 1, y)));
+  }
+  for (int x = 0; x < Lx; ++x) {
+    rT.push_back(yellow_rhoT(c, cell.e(x, y), cell.a(x, y)));
+    rB.push_back(yellow_rhoB(c, cell.e(x, y), cell.a(x, y)));
+  }
+  std::vector<ProjPair> pk = projectors(c, P, rT, rB);
+  for (int x = 0; x < Lx; ++x) {
+    out.g[x] = shaped(pk[x], chi, D);
+    out.y[x] = shaped(pk[Lx + x], chi, D);
   }
   for (int x = 0; x < Lx; ++x)
-    out.r[x] = shaped(projector(c, P, red_rhoT(c, cell.e(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)),
-                                red_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1),
-                                         cell.a(x, y + 1))), chi, p, D);
+    out.K[x] = ket_stage(c, cell.e(x, y), cell.a(x, y), out.g[(x + Lx - 1) % Lx], out.y[x], out.g[x]);
+  // bra stage: teal and red of every row, batched
+  rT.clear();
+  rB.clear();
+  for (int x = 0; x < Lx; ++x) {
+    int xp = (x + 1) % Lx;
+    rT.push_back(teal_rhoT(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+    rB.push_back(teal_rhoB(c, cell.e(xp, y), cell.a(xp, y), out.K[xp], cell.e(xp, y + 1), cell.a(xp, y + 1)));
+  }
+  for (int x = 0; x < Lx; ++x) {
+    rT.push_back(red_rhoT(c, cell.e(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+    rB.push_back(red_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+  }
+  std::vector<ProjPair> pb = projectors(c, P, rT, rB);
+  for (int x = 0; x < Lx; ++x) {
+    out.t[x] = shaped(pb[x], chi, D);
+    out.r[x] = shaped(pb[Lx + x], chi, p, D);
+  }
 }
 
 void left_move(Ctx& c, const Params& P, Cell& cell) {
@@ -517,38 +771,61 @@ static Tensor corner_BL(Ctx& c, const Tensor& T4, const Tensor& C4t, const Tenso
   return mat(einsum(c, "hevbsur,swvez->buwrzh", W, A), 3);   // [(b,u,w), (r,z,h)]
 }
 
-std::vector<EnergyTerm> energy_terms(Ctx& c, const Params& P, Cell& cell, const double* h_nn,
-                                     const double* h_diag) {
+EnergyOps energy_ops(Ctx& c, const Params& P, const double* h_nn, const double* h_diag) {
   const int p = P.p;
   std::vector<OpTerm> tn = decompose(p, h_nn), td = decompose(p, h_diag);
-  // operator list: index 0 = identity
+  // operator list: index 0 = identity; operators equal up to a factor share one
+  // slot (Heisenberg: every factor of every bond), so corners are built once
   std::vector<std::vector<double>> ops;
   std::vector<double> I(p * p, 0.0);
   for (int i = 0; i < p; ++i) I[i * p + i] = 1.0;
   ops.push_back(I);
-  struct Bond { int o1, o2; };   // indices into ops
-  std::vector<std::pair<int, int>> nnp, dgp;
+  auto intern = [&](const std::vector<double>& O, double& scale) -> int {
+    int im = 0;
+    for (int i = 1; i < (int)O.size(); ++i)
+      if (std::fabs(O[i]) > std::fabs(O[im])) im = i;
+    scale = O[im];
+    std::vector<double> v(O.size());
+    for (size_t i = 0; i < O.size(); ++i) v[i] = O[i] / scale;
+    for (size_t j = 1; j < ops.size(); ++j) {
+      double d = 0;
+      for (size_t i = 0; i < v.size(); ++i) d = std::max(d, std::fabs(v[i] - ops[j][i]));
+      if (d < 1e-12) return (int)j;
+    }
+    ops.push_back(v);
+    return (int)ops.size() - 1;
+  };
+  EnergyOps E;
+  std::vector<EnergyOps::Pair>& nnp = E.nn;
+  std::vector<EnergyOps::Pair>& dgp = E.diag;
   for (auto& t : tn) {
-    ops.push_back(t.O); int a = (int)ops.size() - 1;
-    ops.push_back(t.Q); int b = (int)ops.size() - 1;
-    nnp.push_back({a, b});
+    double sa, sb;
+    int a = intern(t.O, sa), b = intern(t.Q, sb);
+    nnp.push_back({a, b, sa * sb});
   }
   for (auto& t : td) {
-    ops.push_back(t.O); int a = (int)ops.size() - 1;
-    ops.push_back(t.Q); int b = (int)ops.size() - 1;
-    dgp.push_back({a, b});
+    double sa, sb;
+    int a = intern(t.O, sa), b = intern(t.Q, sb);
+    dgp.push_back({a, b, sa * sb});
   }
-  std::vector<Tensor> opd(ops.size());
+  E.op.resize(ops.size());
   for (size_t i = 0; i < ops.size(); ++i) {
     bool t = c.tape.active;
     c.tape.active = false;
-    opd[i] = from_host(c, {p, p}, ops[i].data());
+    E.op[i] = from_host(c, {p, p}, ops[i].data());
     c.tape.active = t;
   }
+  return E;
+}
+
+std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const EnergyOps& E, int x, int y) {
+  const std::vector<Tensor>& opd = E.op;
+  const std::vector<EnergyOps::Pair>& nnp = E.nn;
+  const std::vector<EnergyOps::Pair>& dgp = E.diag;
+  const size_t nops = opd.size();
   std::vector<EnergyTerm> terms;
   const double inv_n = 1.0 / (cell.Lx * cell.Ly);
-  for (int x = 0; x < cell.Lx; ++x)
-    for (int y = 0; y < cell.Ly; ++y) {
+  {
       SiteEnv& eTL = cell.e(x, y);
       SiteEnv& eTR = cell.e(x, y + 1);
       SiteEnv& eBR = cell.e(x + 1, y + 1);
@@ -565,7 +842,7 @@ std::vector<EnergyTerm> energy_terms(Ctx& c, const Params& P, Cell& cell, const 
       const Tensor& aTR = cell.a(x, y + 1);
       const Tensor& aBR = cell.a(x + 1, y + 1);
       const Tensor& aBL = cell.a(x + 1, y);
-      std::vector<Tensor> cTL(ops.size()), cTR(ops.size()), cBR(ops.size()), cBL(ops.size());
+      std::vector<Tensor> cTL(nops), cTR(nops), cBR(nops), cBL(nops);
       auto kTL = [&](int o) -> Tensor& {
         if (!cTL[o].data) cTL[o] = corner_TL(c, eTL[C1], T1L, T4T, o ? einsum(c, "ts,suldr->tuldr", opd[o], aTL) : aTL, aTL);
         return cTL[o];
@@ -596,16 +873,18 @@ std::vector<EnergyTerm> energy_terms(Ctx& c, const Params& P, Cell& cell, const 
       Tensor den = dot(c, Htop(0, 0), Hbot(0, 0));
       // nearest-neighbour bonds, half weight each (every bond lies in two patches)
       for (auto& pr : nnp) {
-        int o = pr.first, q = pr.second;
-        terms.push_back({dot(c, Htop(o, q), Hbot(0, 0)), den, 0.5 * inv_n});   // top    (TL, TR)
-        terms.push_back({dot(c, Htop(0, 0), Hbot(o, q)), den, 0.5 * inv_n});   // bottom (BL, BR)
-        terms.push_back({dot(c, Htop(o, 0), Hbot(q, 0)), den, 0.5 * inv_n});   // left   (TL, BL)
-        terms.push_back({dot(c, Htop(0, o), Hbot(0, q)), den, 0.5 * inv_n});   // right  (TR, BR)
+        int o = pr.a, q = pr.b;
+        double w = 0.5 * inv_n * pr.w;
+        terms.push_back({dot(c, Htop(o, q), Hbot(0, 0)), den, w});   // top    (TL, TR)
+        terms.push_back({dot(c, Htop(0, 0), Hbot(o, q)), den, w});   // bottom (BL, BR)
+        terms.push_back({dot(c, Htop(o, 0), Hbot(q, 0)), den, w});   // left   (TL, BL)
+        terms.push_back({dot(c, Htop(0, o), Hbot(0, q)), den, w});   // right  (TR, BR)
       }
       for (auto& pr : dgp) {
-        int o = pr.first, q = pr.second;
-        terms.push_back({dot(c, Htop(o, 0), Hbot(0, q)), den, inv_n});         // TL - BR
-        terms.push_back({dot(c, Htop(0, o), Hbot(q, 0)), den, inv_n});         // TR - BL
+        int o = pr.a, q = pr.b;
+        double w = inv_n * pr.w;
+        terms.push_back({dot(c, Htop(o, 0), Hbot(0, q)), den, w});   // TL - BR
+        terms.push_back({dot(c, Htop(0, o), Hbot(q, 0)), den, w});   // TR - BL
       }
     }
   return terms;

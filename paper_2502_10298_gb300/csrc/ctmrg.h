@@ -30,6 +30,7 @@ struct Params {
   double cutoff = 1e-8;       // relative cutoff on the projector singular values
   double gram_cutoff = 1e-15; // relative cutoff on Gram eigenvalues (reduction)
   double eps_l = 1e-36;       // Lorentzian broadening (relative to s_max^4)
+  bool mixed = false;         // mixed mode: FP32 contractions, randomized projectors
 };
 
 struct ProjPair {
@@ -63,12 +64,21 @@ void move(Ctx& c, const Params& P, Cell& cell, int dir);
 // environment from the neighbours' double layers, padded to chi
 void init_env(Ctx& c, const Params& P, Cell& cell);
 
-// per-site energy pieces: returns the list of (numerator, denominator, weight)
+// energy pieces of one 2x2 patch: list of (numerator, denominator, weight),
+// E = sum over patches and terms of w * num / den
 struct EnergyTerm {
   Tensor num, den;
   double w;
 };
-std::vector<EnergyTerm> energy_terms(Ctx& c, const Params& P, Cell& cell, const double* h_nn,
-                                     const double* h_diag);
+// bond operators split into one-site factors (operator-Schmidt decomposition);
+// factors equal up to a scale share one slot, slot 0 is the identity
+struct EnergyOps {
+  struct Pair { int a, b; double w; };
+  std::vector<Tensor> op;          // [p, p] device matrices
+  std::vector<Pair> nn, diag;
+};
+EnergyOps energy_ops(Ctx& c, const Params& P, const double* h_nn, const double* h_diag);
+// patch with top-left site (x, y)
+std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const EnergyOps& E, int x, int y);
 
 }  // namespace sctm

@@ -4,8 +4,21 @@
 
 namespace sctm {
 
+// fp32_compute: operands rounded to FP32 on load, FP32 accumulation (mixed mode)
 template <typename T>
-void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s);
+void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute);
+
+// Tensor-core form of the same contraction (mixed mode): operands split into
+// TF32 hi/lo pairs, 3xTF32 tcgen05 MMAs with FP32 accumulation, FP64 output.
+// scratch: tc_scratch_floats(d) floats, 128-byte aligned; status: device word
+// set to -2 if a pipeline wait timed out.
+bool tc_eligible(const ContractDesc& d);
+size_t tc_scratch_floats(const ContractDesc& d);
+void launch_contract_tc(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
+                        float* scratch, int* status);
+
+// deterministic N(0,1) test matrix (counter-based hash + Box-Muller), rows x cols
+void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s);
 
 // Batched SVD of m x n row-major matrices (m >= n): M = U diag(S) V^T with
 // U m x n, V n x n, S descending.

@@ -2,6 +2,7 @@
 // scaling, spectrum maps, sign fixing, max-abs rescaling and dot products.
 #include "common.h"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sctm {
 
@@ -31,6 +32,7 @@ template <typename T>
 void launch_copy(const Group& g, T alpha, const T* in, T beta, T* out, cudaStream_t s) {
   long long total = g.total();
   if (total == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   copy_kernel<T><<<grid_for(total), kThreads, 0, s>>>(g, total, alpha, in, beta, out);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -51,6 +53,7 @@ void launch_scale_rc(int batch, int rows, int cols, double* X, const double* v, 
                      cudaStream_t s) {
   long long total = (long long)batch * rows * cols;
   if (total == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   scale_rc_kernel<<<grid_for(total), kThreads, 0, s>>>(batch, rows, cols, X, v, vstride, row);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -129,6 +132,7 @@ void launch_svd_adj_inner(int n, const double* S, const double* J, const double*
                           double* inner, double eps, cudaStream_t s) {
   long long total = (long long)n * n;
   if (total == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   svd_adj_inner_kernel<<<grid_for(total), kThreads, 0, s>>>(n, S, J, K, Sbar, inner, eps);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -227,6 +231,7 @@ __global__ void maxabs_final_scale_kernel(long long n, double* X, long long stri
 void launch_rescale(int batch, long long n, double* X, long long stride, double* scale, long long* argmax,
                     double* partial, cudaStream_t s) {
   if (batch == 0 || n == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   maxabs_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, X, stride, partial);
   SCTM_CUDA(cudaGetLastError());
   maxabs_final_scale_kernel<<<batch, 1024, 0, s>>>(n, X, stride, partial, scale, argmax);
@@ -259,6 +264,7 @@ __global__ void dot_final_kernel(int batch, const double* partial, double* out) 
 void launch_dot(int batch, long long n, const double* x, const double* y, long long stride, double* out,
                 double* partial, cudaStream_t s) {
   if (batch == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   dot_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, x, y, stride, partial);
   SCTM_CUDA(cudaGetLastError());
   dot_final_kernel<<<(batch + 127) / 128, 128, 0, s>>>(batch, partial, out);
@@ -281,6 +287,30 @@ void launch_fill(long long n, double v, double* x, cudaStream_t s) {
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s) {
   if (n == 0) return;
   axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// SplitMix64 finaliser as a counter-based generator; two uniforms -> one normal
+__device__ inline unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(long long n, unsigned long long seed, double* X) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    unsigned long long a = mix64(seed ^ (2 * (unsigned long long)e)), b = mix64(seed ^ (2 * (unsigned long long)e + 1));
+    double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740994.0);   // (0, 1]
+    double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    X[e] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s) {
+  long long n = rows * cols;
+  if (n == 0) return;
+  gaussian_kernel<<<grid_for(n), kThreads, 0, s>>>(n, seed, X);
   SCTM_CUDA(cudaGetLastError());
 }
 

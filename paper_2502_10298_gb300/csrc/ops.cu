@@ -179,7 +179,14 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
   ContractDesc d = plan(sp, A, B, C);
   d.alpha = alpha;
   d.beta = beta;
-  launch_contract<double>(d, A.data, B.data, C.data, c.stream);
+  if (c.fp32_compute && c.tensor_cores && tc_eligible(d)) {
+    size_t mk = c.arena.mark();
+    float* scratch = reinterpret_cast<float*>(c.arena.alloc((long long)(tc_scratch_floats(d) + 1) / 2));
+    launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32);
+    c.arena.release(mk);   // stream-ordered: later work on the stream reuses it after the GEMM
+  } else {
+    launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute);
+  }
   if (!record || !c.tape.active || !C.grad) return;
   std::string sa = sp.c + "," + sp.b + "->" + sp.a;
   std::string sb = sp.a + "," + sp.c + "->" + sp.b;

@@ -18,6 +18,8 @@ struct Ctx {
   int* svd_status = nullptr;     // per-call SVD sweep counts (persistent, device)
   int svd_status_cap = 0;
   bool svd_failed = false;
+  bool fp32_compute = false;     // mixed mode: contractions in FP32 arithmetic
+  bool tensor_cores = true;      // mixed mode: large contractions on tcgen05 (3xTF32)
 
   // new contiguous tensor of the given shape; gradient buffer (zeroed) when taping
   Tensor empty(std::initializer_list<int> shape);

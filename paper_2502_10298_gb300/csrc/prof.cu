@@ -1,0 +1,77 @@
+// Per-kernel-family event timing (see prof.h).
+#include <mutex>
+#include <vector>
+
+#include "common.h"
+#include "prof.h"
+
+namespace sctm {
+
+namespace {
+struct Rec {
+  cudaEvent_t a, b;
+  int fam;
+  double flops, bytes;
+};
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+size_t g_used = 0;
+bool g_on = false;
+std::mutex g_mu;
+
+cudaEvent_t take() {
+  if (g_used < g_pool.size()) return g_pool[g_used++];
+  cudaEvent_t e;
+  SCTM_CUDA(cudaEventCreate(&e));
+  g_pool.push_back(e);
+  ++g_used;
+  return e;
+}
+}  // namespace
+
+void prof_enable(bool on) {
+  std::lock_guard<std::mutex> l(g_mu);
+  g_on = on;
+  g_recs.clear();
+  g_used = 0;
+}
+
+bool prof_enabled() { return g_on; }
+
+ProfScope::ProfScope(int family, cudaStream_t s, double flops, double bytes) : fam(family), st(s) {
+  if (!g_on) return;
+  std::lock_guard<std::mutex> l(g_mu);
+  Rec r;
+  r.a = take();
+  r.b = take();
+  r.fam = family;
+  r.flops = flops;
+  r.bytes = bytes;
+  SCTM_CUDA(cudaEventRecord(r.a, s));
+  slot = (int)g_recs.size();
+  g_recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> l(g_mu);
+  cudaEventRecord(g_recs[slot].b, st);
+}
+
+void prof_collect(double* out) {
+  std::lock_guard<std::mutex> l(g_mu);
+  for (int i = 0; i < PF_N * 4; ++i) out[i] = 0;
+  for (auto& r : g_recs) {
+    SCTM_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0;
+    SCTM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    out[r.fam * 4 + 0] += ms;
+    out[r.fam * 4 + 1] += 1;
+    out[r.fam * 4 + 2] += r.flops;
+    out[r.fam * 4 + 3] += r.bytes;
+  }
+  g_recs.clear();
+  g_used = 0;
+}
+
+}  // namespace sctm

@@ -1,0 +1,25 @@
+// Optional per-kernel-family timing with CUDA events on the launching stream.
+// Disabled by default; when enabled every kernel launch of a family is
+// bracketed by two events, and the caller reads summed device times, launch
+// counts and algorithmic flop / byte counts per family.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sctm {
+
+enum ProfFamily { PF_CONTRACT = 0, PF_SVD = 1, PF_MISC = 2, PF_N = 3 };
+
+void prof_enable(bool on);
+bool prof_enabled();
+// out: PF_N rows of {milliseconds, launches, flops, bytes}
+void prof_collect(double* out);
+
+struct ProfScope {
+  ProfScope(int family, cudaStream_t s, double flops, double bytes);
+  ~ProfScope();
+  int fam;
+  cudaStream_t st;
+  int slot = -1;
+};
+
+}  // namespace sctm

@@ -139,3 +139,36 @@ def test_neel_and_ising_exact(S):
         s.init(torch.tensor(A, device="cuda"))
         s.sweeps(2)
         assert abs(s.energy(H, 0.5 * H) - (-0.5 + 0.25)) < 1e-12
+
+
+@pytest.mark.parametrize("m,n", [(7, 7), (40, 40), (100, 60), (300, 256)])
+def test_jacobi_svd_against_lapack(S, m, n):
+    """Singular values to 1e-13 relative; U S V^T reproduces M; U, V orthonormal."""
+    rng = np.random.default_rng(m + n)
+    M = rng.standard_normal((m, n)) * np.logspace(0, -6, n)[None, :]
+    with S.SplitCTMRG(1, 1, 2, 2, 4) as s:
+        U, Sv, V = S.sctm_svd(s.h, torch.tensor(M, device="cuda"))
+    U, Sv, V = U.cpu().numpy(), Sv.cpu().numpy(), V.cpu().numpy()
+    ref = np.linalg.svd(M, compute_uv=False)
+    assert np.allclose(Sv, ref, rtol=1e-12, atol=1e-14 * ref[0])
+    assert np.abs(U * Sv[None, :] @ V.T - M).max() < 1e-13 * ref[0]
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-13
+    assert np.abs(U.T @ U - np.eye(n)).max() < 1e-11
+
+
+@pytest.mark.parametrize("Lx,Ly,D,chi", [(1, 1, 3, 9), (2, 2, 3, 9)])
+def test_mixed_mode_energy_and_gradient(S, Lx, Ly, D, chi):
+    """precision=1 (FP32 contractions, randomized projectors where alpha > 2 chi):
+    energy within 1e-6 per site and gradient within 1e-4 (norm) of the FP64 oracle."""
+    A = _near(Lx, Ly, D, 0.3, seed=21)
+    h, hd = (HR, None) if Lx == 1 else (H, 0.5 * H)
+    sweeps = 2
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, precision=1) as s:
+        e, g = s.energy_grad(torch.tensor(A, device="cuda"), sweeps, h, hd)
+    Ao = torch.tensor(A).requires_grad_(True)
+    Ac = [[Ao[x, y] for y in range(Ly)] for x in range(Lx)]
+    eo = En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, sweeps), h, hd)
+    eo.backward()
+    assert abs(e - float(eo)) < 1e-6
+    rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
+    assert rel < 1e-4, rel
