@@ -105,10 +105,19 @@ class ClockSampler:
 
 
 def cpu_baseline(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
-    """Time the FP64 oracle on a bounded sample of the same workload: as many
-    single-column left moves (with every projector) as fit in ~budget_s, then
-    scale to one evaluation = (init +) 4*Ly*sweeps column moves forward, the
-    same again recomputed plus ~2x for the reverse pass (autograd)."""
+    """Time the FP64 oracle on a bounded sample of the same workload and scale
+    it to one energy+gradient evaluation.
+
+    Sample: (1) the oracle's initial environment; (2) single-column projector
+    stages of a left move (every colour's rho networks, decompositions and the
+    absorption), as many as fit in about half the budget; (3) one product of
+    two closed enlarged corners, the (chi D^2)^3 contraction the oracle's 2x2
+    energy is made of, on matrices of that exact shape.  Scaling: forward =
+    init + 4 * sweeps moves x Ly columns + the energy (per patch the oracle
+    performs 50 such corner products: two closed-closed, two with both physical
+    pairs open (p^4 = 16 each) and four with one open pair (p^2 = 4 each));
+    one evaluation = forward + reverse, the reverse counted as twice the
+    forward (reverse-mode autograd)."""
     import torch
     from oracle import ctmrg as C
     torch.set_num_threads(os.cpu_count() or 1)
@@ -117,22 +126,32 @@ def cpu_baseline(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
     env = C.initial_env(Ac, c["chi"])
     t_init = time.perf_counter() - t0
     n, t_col = 0, 0.0
-    while t_col < budget_s and n < 8:
+    while t_col < budget_s / 2 and n < 8:
         t1 = time.perf_counter()
         with torch.no_grad():
             C.split_column_projectors(Ac, env, n % c["Ly"], c["chi"])
         t_col += time.perf_counter() - t1
         n += 1
     per_col = t_col / n
+    N = c["chi"] * c["D"] ** 2
+    g = torch.Generator().manual_seed(0)
+    X = torch.randn((N, N), dtype=torch.float64, generator=g)
+    Y = torch.randn((N, N), dtype=torch.float64, generator=g)
+    t1 = time.perf_counter()
+    torch.einsum("ra,rb->ab", X, Y)
+    t_prod = time.perf_counter() - t1
+    del X, Y
     moves = 4 * sweeps
-    cols_per_move = c["Ly"]  # left/right moves; top/bottom use Lx rows (2x2 cell: same)
-    fwd = t_init + moves * cols_per_move * per_col
-    t_eval = fwd * 4.0   # forward + checkpointed recompute + reverse (~2x forward)
+    cols_per_move = c["Ly"]  # left/right moves; top/bottom use Lx rows (square cells here)
+    n_patch = c["Lx"] * c["Ly"]
+    fwd = t_init + moves * cols_per_move * per_col + 50 * n_patch * t_prod
+    t_eval = 3.0 * fwd
     return {"value": 1.0 / t_eval, "unit": "evals/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{n} single-column projector stages of a left move at {name} "
-                      f"({per_col:.2f} s each) + initial environment ({t_init:.2f} s) on the host, "
-                      f"scaled to one energy+gradient evaluation as 4x the forward "
-                      f"({moves} moves x {cols_per_move} columns)"}
+            "sample": f"oracle initial environment ({t_init:.2f} s), {n} single-column projector stages of a "
+                      f"left move ({per_col:.2f} s each) and one {N}^3 closed-corner product "
+                      f"({t_prod:.2f} s) at {name} on the host; scaled to one energy+gradient evaluation "
+                      f"as 3x the forward ({moves} moves x {cols_per_move} columns + {50 * n_patch} corner "
+                      f"products of the 2x2 energy)"}
 
 
 def run_reference(args):
@@ -162,9 +181,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg4")
     ap.add_argument("--sweeps", type=int, default=None)
+    ap.add_argument("--precision", type=int, default=None,
+                    help="0 FP64, 1 mixed (3xTF32 tensor cores), 2 mixed on CUDA cores; default per workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--workspace-gb", type=float, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -185,7 +207,9 @@ def main():
     At = torch.tensor(A, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    s = S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], workspace_bytes=args_ws(c))
+    prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
+    s = S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec,
+                     workspace_bytes=args_ws(c, args.workspace_gb))
 
     def step():
         return s.energy_grad(At, sweeps, h_nn, h_diag)
@@ -235,25 +259,39 @@ def main():
                "d2h_bytes_per_step": int(A.nbytes) + 8}
 
     peaks, src = load_peaks()
+    tot_ms = sum(v["ms"] for v in prof.values())
+    fams = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                "share_of_device_time": v["ms"] / tot_ms if tot_ms else None,
+                "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else 0.0}
+            for k, v in prof.items()}
     fam = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[fam]
-    tot_ms = sum(v["ms"] for v in prof.values())
     achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else 0.0
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": fam,
-            "share_of_device_time": p["ms"] / tot_ms if tot_ms else None,
-            "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM); no FP64 figure in MEASURED_PEAKS.json",
-            "families": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                             "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else 0.0}
-                         for k, v in prof.items()}}
+    if fam == "tensor":
+        # TF32 tensor peak: the measured bf16 figure (sustained: the kernel runs inside a long step)
+        # times the nominal TF32/BF16 ratio 1.1/2.25; achieved counts the algorithmic 2MNK only,
+        # while the 3xTF32 split executes three tensor products per multiply-add
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        peak = bf16 * 1.1 / 2.25
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "tc_gemm_kernel (3xTF32 tcgen05 contraction)",
+                "peak_source": f"TF32 = {src} bf16 sustained x 1.1/2.25 (nominal ratio)",
+                "tensor_pipe_frac": 3.0 * achieved / peak}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": fam,
+                "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM); no FP64 figure measured"}
+    roof["share_of_device_time"] = p["ms"] / tot_ms if tot_ms else None
+    roof["families"] = fams
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(args.config, c, A, h_nn, h_diag, sweeps, budget_s=args.cpu_budget)
     launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "l2": "flushed (256 MiB write) before every step",
+            "vs_baseline": None, "dtype": {0: "f64", 1: "tf32x3 (f32 accumulate) + f64", 2: "f32 + f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": desc, "precision": prec, "l2": "flushed (256 MiB write) before every step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "energy_per_site": e_val, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu,
@@ -266,9 +304,14 @@ def main():
     return 0
 
 
-def args_ws(c):
-    # workspace: checkpoints + one taped sweep; generous on a 280 GB part
-    return int(min(200, max(4, (c["chi"] * c["D"]) ** 2 * c["p"] * 8 * 600 / 2**30)) * 2**30)
+def args_ws(c, gb=None):
+    """Device workspace: one taped 2x2 patch of the energy (about 220 enlarged-corner
+    sized buffers of (chi D^2)^2 doubles, gradients included) plus a taped sweep."""
+    if gb:
+        return int(gb * 2**30)
+    n = c["chi"] * c["D"] ** 2
+    need = 220 * n * n * 8 + 16 * 2**30
+    return int(min(240 * 2**30, max(8 * 2**30, need)))
 
 
 if __name__ == "__main__":

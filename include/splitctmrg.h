@@ -61,12 +61,19 @@ typedef struct {
                                as 3xTF32 (operands split into TF32 hi + lo, FP32
                                accumulation), small ones in FP32 on the CUDA cores;
                                projectors from a randomized subspace iteration (2 chi
-                               columns, two power steps) whenever the truncated space
-                               exceeds 2 chi; decompositions in FP64; default cutoff 1e-6.
+                               columns, Cholesky-QR bases, power_steps steps) when the
+                               truncated space exceeds 2 chi and randomized_min;
+                               decompositions and Gram matrices in FP64; default
+                               cutoff 1e-6.
                             2: as 1 with every contraction on the CUDA cores (FP32). */
   double svd_cutoff;     /* relative singular-value cutoff of projectors (<=0: 1e-8) */
   double lorentz_eps;    /* Lorentzian broadening of the SVD adjoint (<=0: 1e-36 s_max^4) */
   size_t workspace_bytes;/* device workspace; 0 = library default          */
+  int power_steps;       /* mixed mode, randomized projectors: power steps, each
+                            Z = orth(M^T Q), Q = orth(M Z) (0: default 2)        */
+  int randomized_min;    /* mixed mode: randomized projectors only when the space
+                            being truncated has at least this dimension (0: 256);
+                            smaller ones use the exact FP64 decomposition        */
 } sctm_config;
 
 /* Create a handle.  stream: a cudaStream_t (NULL = legacy default stream). */
@@ -141,8 +148,8 @@ SCTM_API int sctm_einsum(sctm_handle h, const char* spec, const double* A_dev, c
 
 /* Per-kernel-family timing.  enable=1 starts recording CUDA events around
  * every kernel launch (on the handle's stream); enable=0 stops and writes
- * out[3][4] = {contraction, svd, other} x {device ms, launches, algorithmic
- * flops, algorithmic bytes}.  Not for timed regions of record: the events
+ * out[4][4] = {CUDA-core contraction, svd, other, tensor-core contraction} x
+ * {device ms, launches, algorithmic flops, algorithmic bytes}.  Not for timed regions of record: the events
  * themselves serialise nothing but add host overhead. */
 SCTM_API int sctm_profile(sctm_handle h, int enable, double* out);
 

@@ -57,9 +57,9 @@ def neel_biased_cell(p: int, D: int, seed: int = 0, bias: float = 0.5) -> np.nda
 CONFIGS = {
     "cfg1": dict(Lx=1, Ly=1, p=2, D=2, chi=16, J2=0.0, rotated=True, sweeps=30, bench_sweeps=30),
     "cfg2": dict(Lx=2, Ly=2, p=2, D=4, chi=32, J2=0.0, rotated=False, sweeps=30, bench_sweeps=4),
-    "cfg3": dict(Lx=2, Ly=2, p=2, D=6, chi=72, J2=0.0, rotated=False, sweeps=20, bench_sweeps=2),
-    "cfg4": dict(Lx=2, Ly=2, p=2, D=8, chi=128, J2=0.5, rotated=False, sweeps=10, bench_sweeps=1),
-    "cfg5": dict(Lx=1, Ly=1, p=2, D=10, chi=200, J2=0.0, rotated=True, sweeps=10, bench_sweeps=1),
+    "cfg3": dict(Lx=2, Ly=2, p=2, D=6, chi=72, J2=0.0, rotated=False, sweeps=20, bench_sweeps=2, bench_precision=1),
+    "cfg4": dict(Lx=2, Ly=2, p=2, D=8, chi=128, J2=0.5, rotated=False, sweeps=10, bench_sweeps=1, bench_precision=1),
+    "cfg5": dict(Lx=1, Ly=1, p=2, D=10, chi=200, J2=0.0, rotated=True, sweeps=10, bench_sweeps=1, bench_precision=1),
 }
 
 

@@ -29,7 +29,8 @@ class SctmError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("p", ctypes.c_int), ("D", ctypes.c_int),
                 ("chi", ctypes.c_int), ("precision", ctypes.c_int), ("svd_cutoff", ctypes.c_double),
-                ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t)]
+                ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
+                ("power_steps", ctypes.c_int), ("randomized_min", ctypes.c_int)]
 
 
 _lib = None
@@ -85,9 +86,10 @@ def _hp(a):
 
 
 def sctm_create(Lx, Ly, p, D, chi, precision=0, svd_cutoff=0.0, lorentz_eps=0.0, workspace_bytes=0,
-                stream=None):
+                stream=None, power_steps=0, randomized_min=0):
     lib = load_library()
-    cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes)
+    cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes, power_steps,
+                 randomized_min)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     h = ctypes.c_void_p()
@@ -167,13 +169,13 @@ def sctm_get_env(h, x, y, chi, D):
     return out
 
 
-PROFILE_FAMILIES = ("contract", "svd", "other")
+PROFILE_FAMILIES = ("contract", "svd", "other", "tensor")
 
 
 def sctm_profile(h, enable: bool):
     """enable=True starts per-family event timing; enable=False returns
     {family: dict(ms, launches, flops, bytes)} and stops it."""
-    out = np.zeros(12)
+    out = np.zeros(4 * len(PROFILE_FAMILIES))
     _check(h, _lib.sctm_profile(h, 1 if enable else 0, out.ctypes.data_as(_dp)))
     if enable:
         return None

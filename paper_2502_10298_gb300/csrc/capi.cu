@@ -254,6 +254,9 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     h->c.tensor_cores = (cfg->precision == 1);
     if (P.mixed) P.cutoff = 1e-6;   // FP32 contractions: singular values below ~1e-7 s_max are rounding noise
     if (cfg->svd_cutoff > 0) P.cutoff = cfg->svd_cutoff;
+    SCTM_CHECK(cfg->power_steps >= 0 && cfg->power_steps <= 16, "power_steps must be in [0, 16]");
+    if (cfg->power_steps > 0) P.power_steps = cfg->power_steps;
+    if (cfg->randomized_min > 0) P.randomized_min = cfg->randomized_min;
     if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
     h->c.stream = (cudaStream_t)stream;
     const int chi = P.chi, D = P.D;

@@ -20,19 +20,8 @@ static Tensor no_grad(Tensor t) {
   return t;
 }
 
-// Orthonormal basis of the columns of Y (n x r): eigen-decompose G = Y^T Y
-// (FP64 Jacobi) and return Y W Lambda^-1/2, dropping eigenvalues below
-// 1e-14 lambda_max (numerically dependent directions).  Not taped.
-static Tensor orthonormal_columns(Ctx& c, const Tensor& Y) {
-  const int r = Y.shape[1];
-  Tensor G = einsum(c, "ai,aj->ij", Y, Y);
-  SVDResult e = svd(c, G, 0.0);
-  Tensor w = spectrum_map(c, e.S, r, 1e-14, 0);   // lambda^-1/2
-  Tensor W = scale_dim(c, e.V, 1, w);
-  return einsum(c, "ai,ij->aj", Y, W);
-}
-
-// Batched SVD of equally shaped square matrices (untaped): one kernel launch.
+// Batched SVD of equally shaped square matrices (untaped, noise-level columns
+// exempt from the convergence test): one kernel launch.
 static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
   const int nb = (int)Ms.size();
   std::vector<SVDResult> out(nb);
@@ -42,57 +31,66 @@ static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
   for (int i = 0; i < nb; ++i) copy_into(c, Ms[i], Mb.sub(0, i));
   size_t wn = svd_work_doubles(n, n, nb);
   double* work = wn ? c.arena.alloc((long long)wn) : nullptr;
-  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream);
+  // Gram eigen-solves of the randomized path: eigenvalues below 1e-14 lambda_max
+  // are discarded, so their (noise-level) columns need not converge
+  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 2.0e-29);
   for (int i = 0; i < nb; ++i) out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};
   return out;
 }
 
-// Orthonormal bases of many n_i x r blocks at once (see orthonormal_columns).
+// Contractions of this scope run in FP64 arithmetic even in mixed mode.
+struct Fp64Scope {
+  Ctx& c;
+  bool old;
+  explicit Fp64Scope(Ctx& cx) : c(cx), old(cx.fp32_compute) { c.fp32_compute = false; }
+  ~Fp64Scope() { c.fp32_compute = old; }
+};
+
+// G = Y^T Y in FP64 with the row sum split into chunks (more CTAs for the
+// short, wide Gram products), then reduced.
+static Tensor gram64(Ctx& c, const Tensor& Y) {
+  Fp64Scope f(c);
+  const int m = Y.shape[0], r = Y.shape[1];
+  int sp = 16;
+  while (sp > 1 && m % sp) --sp;
+  if (sp == 1 || !Y.contiguous()) return einsum(c, "ai,aj->ij", Y, Y);
+  Tensor Y3 = Y.reshape({sp, m / sp, r});
+  Tensor Gs = einsum(c, "sai,saj->sij", Y3, Y3);
+  Tensor ones = c.empty({sp});
+  launch_fill(sp, 1.0, ones.data, c.stream);
+  return einsum(c, "sij,s->ij", Gs, ones);
+}
+
+// Orthonormal (or zero) columns spanning the columns of each Y_i (m_i x r):
+// two passes of Cholesky QR (CholeskyQR2; Yamamoto et al. 2015) with FP64
+// Gram matrices and deflation of dependent columns (pivots below 1e-13 of the
+// largest), Q = Y R^+.  Not taped.
 static std::vector<Tensor> orthonormal_columns_batch(Ctx& c, const std::vector<Tensor>& Ys) {
-  std::vector<Tensor> Gs, out;
-  for (auto& Y : Ys) Gs.push_back(einsum(c, "ai,aj->ij", Y, Y));
-  std::vector<SVDResult> e = svd_batch(c, Gs);
-  for (size_t i = 0; i < Ys.size(); ++i) {
-    const int r = Ys[i].shape[1];
-    Tensor w = spectrum_map(c, e[i].S, r, 1e-14, 0);
-    out.push_back(einsum(c, "ai,ij->aj", Ys[i], scale_dim(c, e[i].V, 1, w)));
+  const int nb = (int)Ys.size();
+  if (nb == 0) return {};
+  const int r = Ys[0].shape[1];
+  std::vector<Tensor> Q = Ys;
+  for (int pass = 0; pass < 2; ++pass) {
+    Tensor Gb = c.empty({nb, r, r}), Tb = c.empty({nb, r, r});
+    for (int i = 0; i < nb; ++i) copy_into(c, gram64(c, Q[i]), Gb.sub(0, i));
+    launch_chol_qr_factor(r, nb, Gb.data, Tb.data, 1e-13, c.stream);
+    for (int i = 0; i < nb; ++i) Q[i] = einsum(c, "ai,ij->aj", Q[i], Tb.sub(0, i));
   }
-  return out;
+  return Q;
 }
 
 // Top-r singular triplets of M = rhoB rhoT (beta x beta, never formed) by
-// randomized subspace iteration with two power steps (Halko, Martinsson,
-// Tropp 2011, Alg. 4.4), in FP64 arithmetic for the small decompositions.
-// Returns U (beta x r), S (r), V (beta x r) with M ~ U S V^T.  Not taped.
+// randomized subspace iteration (Halko, Martinsson, Tropp 2011, Alg. 4.4):
+// Q = orth(M Omega), then `power_steps` times Z = orth(M^T Q), Q = orth(M Z)
+// (a basis after every product keeps the small directions resolvable), and
+// finally B = Q^T M decomposed through its FP64 Gram matrix B B^T = W L W^T:
+// U = Q W, S = L^1/2, V = B^T W S^-1.  Returns U (beta x r), S (r), V (beta x r)
+// with M ~ U S V^T.  Not taped.
 struct Trunc {
   Tensor U, S, V;
 };
-static Trunc randomized_svd(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, int r) {
-  const int b = rhoT.shape[1];
-  Tensor Om = c.empty({b, r});
-  launch_gaussian(b, r, 0x5eedULL + (unsigned long long)b * 131 + r, Om.data, c.stream);
-  Tensor Y = einsum(c, "ab,bj->aj", rhoB, einsum(c, "ab,bj->aj", rhoT, Om));        // M Omega
-  for (int q = 0; q < 2; ++q) {
-    Tensor Q = orthonormal_columns(c, Y);
-    Tensor Z = einsum(c, "ba,bj->aj", rhoT, einsum(c, "ba,bj->aj", rhoB, Q));     // M^T Q
-    Y = einsum(c, "ab,bj->aj", rhoB, einsum(c, "ab,bj->aj", rhoT, Z));            // M M^T Q
-  }
-  Tensor Q = orthonormal_columns(c, Y);                                          // beta x r
-  Tensor Bt = einsum(c, "ba,bj->aj", rhoT, einsum(c, "ba,bj->aj", rhoB, Q));     // M^T Q = B^T
-  Tensor G = einsum(c, "ai,aj->ij", Bt, Bt);                                     // B B^T
-  SVDResult e = svd(c, G, 0.0);                                                  // = W Lambda W^T
-  Trunc t;
-  t.S = spectrum_map(c, e.S, r, 0.0, 1);                                         // sqrt(lambda)
-  // lambda^-1/2; eigenvalues of the FP64 Gram matrix below 1e-14 lambda_max are
-  // rounding noise (singular values below 1e-7 s_max, under every cutoff used)
-  Tensor sinv = spectrum_map(c, e.S, r, 1e-14, 0);
-  t.U = einsum(c, "ai,ij->aj", Q, e.V);                                          // Q W
-  t.V = scale_dim(c, einsum(c, "ai,ij->aj", Bt, e.V), 1, sinv);                  // B^T W S^-1
-  return t;
-}
-
 static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB,
-                                               int r) {
+                                               int r, int power_steps) {
   const size_t nb = rT.size();
   std::vector<Tensor> Y(nb);
   for (size_t i = 0; i < nb; ++i) {
@@ -102,38 +100,51 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
     Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Om));       // M Omega
   }
   std::vector<Tensor> Q = orthonormal_columns_batch(c, Y);
-  for (int q = 0; q < 2; ++q) {   // two power steps
-    for (size_t i = 0; i < nb; ++i) {
-      Tensor Z = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));  // M^T Q
-      Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Z));        // M M^T Q
-    }
+  for (int q = 0; q < power_steps; ++q) {
+    for (size_t i = 0; i < nb; ++i)
+      Y[i] = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));    // M^T Q
+    std::vector<Tensor> Z = orthonormal_columns_batch(c, Y);
+    for (size_t i = 0; i < nb; ++i)
+      Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Z[i]));    // M Z
     Q = orthonormal_columns_batch(c, Y);
   }
   std::vector<Tensor> Bt(nb), G(nb);
   for (size_t i = 0; i < nb; ++i) {
     Bt[i] = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));    // B^T = M^T Q
-    G[i] = einsum(c, "ai,aj->ij", Bt[i], Bt[i]);
+    G[i] = gram64(c, Bt[i]);                                                      // B B^T
   }
   std::vector<SVDResult> e = svd_batch(c, G);
   std::vector<Trunc> out(nb);
   for (size_t i = 0; i < nb; ++i) {
-    out[i].S = spectrum_map(c, e[i].S, r, 0.0, 1);
-    Tensor sinv = spectrum_map(c, e[i].S, r, 1e-14, 0);   // see randomized_svd
+    out[i].S = spectrum_map(c, e[i].S, r, 0.0, 1);                                 // sqrt(lambda)
+    // lambda^-1/2; eigenvalues of the FP64 Gram matrix below 1e-14 lambda_max
+    // are rounding noise (singular values below 1e-7 s_max, under every cutoff)
+    Tensor sinv = spectrum_map(c, e[i].S, r, 1e-14, 0);
     out[i].U = einsum(c, "ai,ij->aj", Q[i], e[i].V);
     out[i].V = scale_dim(c, einsum(c, "ai,ij->aj", Bt[i], e[i].V), 1, sinv);
   }
   return out;
 }
 
-// Reverse pass of a truncated SVD (U_r, S_r, V_r) of M = rhoB rhoT, treating
-// the singular values beyond r as zero (the projector uses the first k < r
-// triplets, so the coupling to the r - k next ones is exact):
-//   M_bar = U X V^T + (U_bar - U J) S^-1 V^T + U S^-1 (V_bar - V K)^T,
+// Reverse pass of a truncated SVD (U_r, S_r, V_r) of M = rhoB rhoT (beta x
+// beta, never formed).  Pairs inside the r computed triplets use the usual
+// broadened coefficients; the coupling of triplet i to the unknown rest of the
+// spectrum is exact: with P = 1 - U U^T, Q = 1 - V V^T, the columns
+//   y_i = (s_i^2 - P M M^T P)^-1 P (s_i u_bar_i + M v_bar_i),
+//   z_i = (s_i^2 - Q M^T M Q)^-1 Q (M^T u_bar_i + s_i v_bar_i)
+// (first-order perturbation theory summed over the complement) are found by
+// column-wise conjugate gradients, which only apply M and M^T.  Then
+//   M_bar = U X V^T + Y V^T + U Z^T,
 //   X = F o (J - J^T) S + diag(S_bar) + S F o (K - K^T), J = U^T U_bar, K = V^T V_bar,
 // applied without forming M_bar:  rhoB_bar += M_bar rhoT^T, rhoT_bar += rhoB^T M_bar.
+// The systems are positive definite for the kept triplets (s_i > s_{r+1});
+// columns without cotangent stay zero.
+static constexpr int kComplementCG = 10;
+
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l) {
   const int k = S.shape[0];
+  const int nb = U.shape[0];
   Tensor gU = no_grad(U), gV = no_grad(V), gS = no_grad(S);
   gU.data = U.grad;
   gV.data = V.grad;
@@ -142,28 +153,47 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
   einsum_into(c, "ai,aj->ij", U, gU, J, 1.0, 0.0, false);
   einsum_into(c, "ai,aj->ij", V, gV, K, 1.0, 0.0, false);
   launch_svd_adj_inner(k, S.data, J.data, K.data, gS.data, X.data, eps_l, c.stream);
-  // 1/s on kept entries, applied as two scalings by s^-1/2
-  Tensor r = c.empty({k});
-  launch_spectrum_map(1, k, k, S.data, r.data, 1e-14, 0, c.stream);
-  Tensor A = c.empty({(int)U.shape[0], k}), Bm = c.empty({(int)V.shape[0], k});
-  // A = (U_bar - U J) S^-1 ; B = (V_bar - V K) S^-1
-  einsum_into(c, "ai,ij->aj", U, J, A, -1.0, 0.0, false);
-  launch_copy<double>([&]() { Group g; g.nd = 2; g.size[0] = U.shape[0]; g.size[1] = k;
-                              g.sa[0] = k; g.sa[1] = 1; g.sc[0] = k; g.sc[1] = 1; return g; }(),
-                      1.0, gU.data, 1.0, A.data, c.stream);
-  einsum_into(c, "ai,ij->aj", V, K, Bm, -1.0, 0.0, false);
-  launch_copy<double>([&]() { Group g; g.nd = 2; g.size[0] = V.shape[0]; g.size[1] = k;
-                              g.sa[0] = k; g.sa[1] = 1; g.sc[0] = k; g.sc[1] = 1; return g; }(),
-                      1.0, gV.data, 1.0, Bm.data, c.stream);
-  launch_scale_rc(1, U.shape[0], k, A.data, r.data, 0, false, c.stream);
-  launch_scale_rc(1, U.shape[0], k, A.data, r.data, 0, false, c.stream);
-  launch_scale_rc(1, V.shape[0], k, Bm.data, r.data, 0, false, c.stream);
-  launch_scale_rc(1, V.shape[0], k, Bm.data, r.data, 0, false, c.stream);
-  // L1 = U X + A
-  Tensor L1 = c.empty({(int)U.shape[0], k});
+  // products with M = rhoB rhoT and M^T on beta x k blocks
+  auto Mx = [&](const Tensor& x) { return einsum(c, "ab,bj->aj", rhoB, einsum(c, "ab,bj->aj", rhoT, x)); };
+  auto MTx = [&](const Tensor& x) { return einsum(c, "ba,bj->aj", rhoT, einsum(c, "ba,bj->aj", rhoB, x)); };
+  auto project = [&](const Tensor& B, Tensor x) {   // x <- (1 - B B^T) x, in place
+    einsum_into(c, "ai,ij->aj", B, einsum(c, "ai,aj->ij", B, x), x, -1.0, 1.0, false);
+    return x;
+  };
+  Tensor s2 = c.empty({k});
+  einsum_into(c, "j,j->j", S, S, s2, 1.0, 0.0, false);   // s_j^2
+  // column-wise CG for (diag(s^2) - B) Y = rhs, B = P op P
+  auto solve = [&](const Tensor& Bas, Tensor rhs, bool left) {
+    Tensor Yv = c.zeros({nb, k});
+    Tensor R = copy(c, rhs);
+    Tensor Pd = copy(c, rhs);
+    Tensor rr = einsum(c, "aj,aj->j", R, R), rr2 = c.empty({k});
+    for (int it = 0; it < kComplementCG; ++it) {
+      Tensor Bp = project(Bas, left ? Mx(MTx(Pd)) : MTx(Mx(Pd)));
+      Tensor Q = scale_dim(c, Pd, 1, s2);
+      launch_axpy(Q.numel(), -1.0, Bp.data, Q.data, c.stream);          // Q = s^2 p - B p
+      Tensor pq = einsum(c, "aj,aj->j", Pd, Q);
+      launch_cg_update(nb, k, Pd.data, Q.data, Yv.data, R.data, rr.data, pq.data, c.stream);
+      einsum_into(c, "aj,aj->j", R, R, rr2, 1.0, 0.0, false);
+      launch_cg_direction(nb, k, Pd.data, R.data, rr2.data, rr.data, c.stream);
+      std::swap(rr, rr2);
+    }
+    return Yv;
+  };
+  // right-hand sides: P (U_bar S + M V_bar), Q (M^T U_bar + V_bar S)
+  Tensor bY = scale_dim(c, gU, 1, S);
+  launch_axpy(bY.numel(), 1.0, Mx(gV).data, bY.data, c.stream);
+  bY = project(U, bY);
+  Tensor bZ = scale_dim(c, gV, 1, S);
+  launch_axpy(bZ.numel(), 1.0, MTx(gU).data, bZ.data, c.stream);
+  bZ = project(V, bZ);
+  Tensor A = solve(U, bY, true);
+  Tensor Bm = solve(V, bZ, false);
+  // L1 = U X + Y
+  Tensor L1 = c.empty({nb, k});
   einsum_into(c, "ai,ij->aj", U, X, L1, 1.0, 0.0, false);
   launch_axpy(L1.numel(), 1.0, A.data, L1.data, c.stream);
-  // rhoB_bar += L1 (V^T rhoT^T) + U (B^T rhoT^T)
+  // rhoB_bar += L1 (V^T rhoT^T) + U (Z^T rhoT^T)
   if (rhoB.grad) {
     Tensor gB = no_grad(rhoB);
     gB.data = rhoB.grad;
@@ -173,7 +203,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
     einsum_into(c, "bj,ja->ba", L1, VR, gB, 1.0, 1.0, false);
     einsum_into(c, "bj,ja->ba", U, BR, gB, 1.0, 1.0, false);
   }
-  // rhoT_bar += (rhoB^T L1) V^T + (rhoB^T U) B^T
+  // rhoT_bar += (rhoB^T L1) V^T + (rhoB^T U) Z^T
   if (rhoT.grad) {
     Tensor gT = no_grad(rhoT);
     gT.data = rhoT.grad;
@@ -194,7 +224,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
 //   K = L_B^T L_T = U S V^T,  P_up = S^-1/2 U^T L_B^T,  P_dn = L_T V S^-1/2,
 // which equals S^-1/2 U~^T rhoB and rhoT V~ S^-1/2 for the full M.
 // Mixed mode with alpha > 2 chi: the chi leading triplets of M come from a
-// randomized subspace iteration (randomized_svd) and the reverse pass uses
+// randomized subspace iteration (randomized_svd_batch) and the reverse pass uses
 // the truncated-SVD adjoint above.
 static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, const Trunc& t) {
   const int k = P.chi;
@@ -228,7 +258,8 @@ static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, c
 }
 
 static bool use_randomized(const Params& P, const Tensor& rhoT) {
-  return P.mixed && std::min(rhoT.shape[0], rhoT.shape[1]) > 2 * P.chi;
+  const int n = std::min(rhoT.shape[0], rhoT.shape[1]);
+  return P.mixed && n > 2 * P.chi && n >= P.randomized_min;
 }
 
 std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB) {
@@ -247,7 +278,7 @@ std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tens
   if (!ri.empty()) {
     bool tap = c.tape.active;
     c.tape.active = false;
-    std::vector<Trunc> t = randomized_svd_batch(c, bT, bB, 2 * P.chi);
+    std::vector<Trunc> t = randomized_svd_batch(c, bT, bB, 2 * P.chi, P.power_steps);
     c.tape.active = tap;
     for (size_t j = 0; j < ri.size(); ++j) out[ri[j]] = finish_randomized(c, P, bT[j], bB[j], t[j]);
   }
@@ -261,7 +292,7 @@ ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rh
   if (use_randomized(P, rhoT)) {
     bool tap = c.tape.active;
     c.tape.active = false;
-    Trunc t = randomized_svd(c, rhoT, rhoB, 2 * k);
+    Trunc t = randomized_svd_batch(c, {rhoT}, {rhoB}, 2 * k, P.power_steps)[0];
     c.tape.active = tap;
     return finish_randomized(c, P, rhoT, rhoB, t);
   }
@@ -604,12 +635,13 @@ void move(Ctx& c, const Params& P, Cell& cell, int dir) {
 // first[P,K,i] = U sqrt(S) and second[i,K2,N] = sqrt(S) V^T, keeping
 // min(chi, rank) values above the cutoff, sign fixed on the columns of U,
 // zero-padded to [chi_P, K, chi] and [chi, K2, chi_N].
-static void split_edge(Ctx& c, const Params& P, const Tensor& T, Tensor& first, Tensor& second, int padP, int padN) {
+// Split a double-layer edge T[prev, ket leg, bra leg, next] into its ket and
+// bra halves from the SVD of ((prev, ket), (bra, next)) truncated to chi:
+// first = U sqrt(S), second = sqrt(S) V^T, each zero-padded to chi.
+static void split_edge_from(Ctx& c, const Params& P, const Tensor& T, const SVDResult& r, Tensor& first,
+                            Tensor& second, int padP, int padN) {
   const int Pd = T.shape[0], Kd = T.shape[1], K2 = T.shape[2], Nd = T.shape[3];
-  const int rows = Pd * Kd, cols = K2 * Nd;
-  SCTM_CHECK(rows == cols, "edge split expects a square matrix");
-  Tensor M = T.reshape({rows, cols});
-  SVDResult r = svd(c, M, P.eps_l);
+  const int rows = Pd * Kd;
   const int k = std::min(P.chi, rows);
   Tensor q = spectrum_map(c, r.S, k, P.cutoff, 1);
   Tensor Uk = r.U, Vk = r.V;
@@ -658,6 +690,10 @@ void init_env(Ctx& c, const Params& P, Cell& cell) {
     copy_into(c, m, v);
     return z;
   };
+  // every edge split of the cell in one batched SVD
+  struct Job { int x, y; const Tensor* T; Key a, b; };
+  std::vector<Job> jobs;
+  std::vector<Tensor> mats;
   for (int x = 0; x < cell.Lx; ++x)
     for (int y = 0; y < cell.Ly; ++y) {
       SiteEnv& e = cell.e(x, y);
@@ -665,18 +701,34 @@ void init_env(Ctx& c, const Params& P, Cell& cell) {
       e[C2] = padC(P_(x - 1, y + 1).c2);
       e[C3] = padC(P_(x + 1, y + 1).c3);
       e[C4] = padC(P_(x + 1, y - 1).c4);
-      split_edge(c, P, P_(x - 1, y).t1, e[T1k], e[T1b], chi, chi);
-      split_edge(c, P, P_(x, y + 1).t2, e[T2k], e[T2b], chi, chi);
-      split_edge(c, P, P_(x + 1, y).t3, e[T3b], e[T3k], chi, chi);
-      split_edge(c, P, P_(x, y - 1).t4, e[T4b], e[T4k], chi, chi);
+      jobs.push_back({x, y, &P_(x - 1, y).t1, T1k, T1b});
+      jobs.push_back({x, y, &P_(x, y + 1).t2, T2k, T2b});
+      jobs.push_back({x, y, &P_(x + 1, y).t3, T3b, T3k});
+      jobs.push_back({x, y, &P_(x, y - 1).t4, T4b, T4k});
     }
+  for (const Job& j : jobs) {
+    const Tensor& T = *j.T;
+    SCTM_CHECK(T.shape[0] * T.shape[1] == T.shape[2] * T.shape[3], "edge split expects a square matrix");
+    mats.push_back(T.reshape({T.shape[0] * T.shape[1], T.shape[2] * T.shape[3]}));
+  }
+  std::vector<SVDResult> rs;
+  for (size_t i0 = 0; i0 < mats.size(); i0 += 64) {   // the batched kernel takes up to 64 matrices
+    std::vector<Tensor> part(mats.begin() + i0, mats.begin() + std::min(mats.size(), i0 + 64));
+    std::vector<SVDResult> pr = svd_many(c, part, P.eps_l);
+    rs.insert(rs.end(), pr.begin(), pr.end());
+  }
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    SiteEnv& e = cell.e(jobs[i].x, jobs[i].y);
+    split_edge_from(c, P, *jobs[i].T, rs[i], e[jobs[i].a], e[jobs[i].b], chi, chi);
+  }
 }
 
 // ------------------------------------------------------------------ energy
 // Two-site operators h[(t_i t_j), (s_i s_j)] are decomposed on the host into
 // sum_k O_k (x) Q_k (operator Schmidt decomposition of a p^2 x p^2 matrix); the
-// 2x2 patch is contracted as four enlarged corners with the ket of a corner
-// replaced by O.A.  Bond value = <H_top(o1,o2), H_bot(o3,o4)> / <H_top(I,I), H_bot(I,I)>.
+// 2x2 patch is contracted as four enlarged corners with the operator O of a
+// corner applied to its site (on the bra side, see half_TL).
+// Bond value = <H_top(o1,o2), H_bot(o3,o4)> / <H_top(I,I), H_bot(I,I)>.
 static void host_svd(int n, std::vector<double> a, std::vector<double>& U, std::vector<double>& S,
                      std::vector<double>& V) {
   // one-sided Jacobi on an n x n host matrix (bond operator, n = p^2)
@@ -745,30 +797,41 @@ static std::vector<OpTerm> decompose(int p, const double* h) {
 
 static Tensor fuse_edge(Ctx& c, const Tensor& a, const Tensor& b, const char* spec) { return einsum(c, spec, a, b); }
 
-// enlarged corners (conventional edges), ket = Ak, bra = A
-static Tensor corner_TL(Ctx& c, const Tensor& C1t, const Tensor& T1, const Tensor& T4, const Tensor& Ak, const Tensor& A) {
+// Enlarged corners (conventional edges): the environment part and the ket
+// layer form an operator-independent half; the bra layer closes it.  A
+// one-site operator O of the energy sits on the bra side, Ab = O^T A, which
+// equals replacing the ket by O A: sum_{s,t} O[t,s] A[s] A[t].
+static Tensor half_TL(Ctx& c, const Tensor& C1t, const Tensor& T1, const Tensor& T4, const Tensor& A) {
   Tensor X = einsum(c, "ab,auwc->buwc", C1t, T1);
   X = einsum(c, "buwc,nvlb->uwcnvl", X, T4);
-  X = einsum(c, "uwcnvl,suldr->wcnvsdr", X, Ak);
-  return mat(einsum(c, "wcnvsdr,swvez->crznde", X, A), 3);   // [(c,r,z), (n,d,e)]
+  return einsum(c, "uwcnvl,suldr->wcnvsdr", X, A);
 }
-static Tensor corner_TR(Ctx& c, const Tensor& T1, const Tensor& C2t, const Tensor& T2, const Tensor& Ak, const Tensor& A) {
+static Tensor finish_TL(Ctx& c, const Tensor& X, const Tensor& Ab) {
+  return mat(einsum(c, "wcnvsdr,swvez->crznde", X, Ab), 3);   // [(c,r,z), (n,d,e)]
+}
+static Tensor half_TR(Ctx& c, const Tensor& T1, const Tensor& C2t, const Tensor& T2, const Tensor& A) {
   Tensor Y = einsum(c, "auwc,cf->auwf", T1, C2t);
   Y = einsum(c, "auwf,frzg->auwrzg", Y, T2);
-  Y = einsum(c, "auwrzg,suldr->awzgsld", Y, Ak);
-  return mat(einsum(c, "awzgsld,swvez->alvdeg", Y, A), 3);   // [(a,l,v), (d,e,g)]
+  return einsum(c, "auwrzg,suldr->awzgsld", Y, A);
 }
-static Tensor corner_BR(Ctx& c, const Tensor& T2, const Tensor& C3t, const Tensor& T3, const Tensor& Ak, const Tensor& A) {
+static Tensor finish_TR(Ctx& c, const Tensor& Y, const Tensor& Ab) {
+  return mat(einsum(c, "awzgsld,swvez->alvdeg", Y, Ab), 3);   // [(a,l,v), (d,e,g)]
+}
+static Tensor half_BR(Ctx& c, const Tensor& T2, const Tensor& C3t, const Tensor& T3, const Tensor& A) {
   Tensor Z = einsum(c, "frzg,gh->frzh", T2, C3t);
   Z = einsum(c, "frzh,hedm->frzedm", Z, T3);
-  Z = einsum(c, "frzedm,suldr->fzemsul", Z, Ak);
-  return mat(einsum(c, "fzemsul,swvez->uwflvm", Z, A), 3);   // [(u,w,f), (l,v,m)]
+  return einsum(c, "frzedm,suldr->fzemsul", Z, A);
 }
-static Tensor corner_BL(Ctx& c, const Tensor& T4, const Tensor& C4t, const Tensor& T3, const Tensor& Ak, const Tensor& A) {
+static Tensor finish_BR(Ctx& c, const Tensor& Z, const Tensor& Ab) {
+  return mat(einsum(c, "fzemsul,swvez->uwflvm", Z, Ab), 3);   // [(u,w,f), (l,v,m)]
+}
+static Tensor half_BL(Ctx& c, const Tensor& T4, const Tensor& C4t, const Tensor& T3, const Tensor& A) {
   Tensor W = einsum(c, "hedm,mn->hedn", T3, C4t);
   W = einsum(c, "hedn,nvlb->hedvlb", W, T4);
-  W = einsum(c, "hedvlb,suldr->hevbsur", W, Ak);
-  return mat(einsum(c, "hevbsur,swvez->buwrzh", W, A), 3);   // [(b,u,w), (r,z,h)]
+  return einsum(c, "hedvlb,suldr->hevbsur", W, A);
+}
+static Tensor finish_BL(Ctx& c, const Tensor& W, const Tensor& Ab) {
+  return mat(einsum(c, "hevbsur,swvez->buwrzh", W, Ab), 3);   // [(b,u,w), (r,z,h)]
 }
 
 EnergyOps energy_ops(Ctx& c, const Params& P, const double* h_nn, const double* h_diag) {
@@ -843,20 +906,26 @@ std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const 
       const Tensor& aBR = cell.a(x + 1, y + 1);
       const Tensor& aBL = cell.a(x + 1, y);
       std::vector<Tensor> cTL(nops), cTR(nops), cBR(nops), cBL(nops);
+      Tensor hTL, hTR, hBR, hBL;   // operator-independent halves, built once
+      auto bra = [&](int o, const Tensor& a) { return o ? einsum(c, "ts,tuldr->suldr", opd[o], a) : a; };
       auto kTL = [&](int o) -> Tensor& {
-        if (!cTL[o].data) cTL[o] = corner_TL(c, eTL[C1], T1L, T4T, o ? einsum(c, "ts,suldr->tuldr", opd[o], aTL) : aTL, aTL);
+        if (!hTL.data) hTL = half_TL(c, eTL[C1], T1L, T4T, aTL);
+        if (!cTL[o].data) cTL[o] = finish_TL(c, hTL, bra(o, aTL));
         return cTL[o];
       };
       auto kTR = [&](int o) -> Tensor& {
-        if (!cTR[o].data) cTR[o] = corner_TR(c, T1R, eTR[C2], T2T, o ? einsum(c, "ts,suldr->tuldr", opd[o], aTR) : aTR, aTR);
+        if (!hTR.data) hTR = half_TR(c, T1R, eTR[C2], T2T, aTR);
+        if (!cTR[o].data) cTR[o] = finish_TR(c, hTR, bra(o, aTR));
         return cTR[o];
       };
       auto kBR = [&](int o) -> Tensor& {
-        if (!cBR[o].data) cBR[o] = corner_BR(c, T2B, eBR[C3], T3R, o ? einsum(c, "ts,suldr->tuldr", opd[o], aBR) : aBR, aBR);
+        if (!hBR.data) hBR = half_BR(c, T2B, eBR[C3], T3R, aBR);
+        if (!cBR[o].data) cBR[o] = finish_BR(c, hBR, bra(o, aBR));
         return cBR[o];
       };
       auto kBL = [&](int o) -> Tensor& {
-        if (!cBL[o].data) cBL[o] = corner_BL(c, T4B, eBL[C4], T3L, o ? einsum(c, "ts,suldr->tuldr", opd[o], aBL) : aBL, aBL);
+        if (!hBL.data) hBL = half_BL(c, T4B, eBL[C4], T3L, aBL);
+        if (!cBL[o].data) cBL[o] = finish_BL(c, hBL, bra(o, aBL));
         return cBL[o];
       };
       std::map<std::pair<int, int>, Tensor> top, bot;

@@ -31,6 +31,8 @@ struct Params {
   double gram_cutoff = 1e-15; // relative cutoff on Gram eigenvalues (reduction)
   double eps_l = 1e-36;       // Lorentzian broadening (relative to s_max^4)
   bool mixed = false;         // mixed mode: FP32 contractions, randomized projectors
+  int power_steps = 2;        // randomized projectors: power steps (mixed mode)
+  int randomized_min = 256;   // randomized projectors only when the truncated space has >= this dimension
 };
 
 struct ProjPair {

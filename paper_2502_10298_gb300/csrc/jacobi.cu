@@ -99,7 +99,7 @@ __device__ int jacobi_core(int m, int n, double* W, double* V, int max_sweeps, d
 __global__ void __launch_bounds__(kSvdThreads)
 svd_kernel(int m, int n, const double* __restrict__ M, double* __restrict__ U, double* __restrict__ S,
            double* __restrict__ V, double* __restrict__ work, int* __restrict__ status, int max_sweeps,
-           double tol, int in_smem) {
+           double tol, double noise_rel, int in_smem) {
   extern __shared__ double sm[];
   __shared__ int flag;
   const long long mn = (long long)m * n, nn = (long long)n * n;
@@ -126,8 +126,8 @@ svd_kernel(int m, int n, const double* __restrict__ M, double* __restrict__ U, d
     if ((threadIdx.x & 31) == 0) atomicAdd(&fro, a);
   }
   __syncthreads();
-  // a column whose norm^2 is below (64 eps)^2 ||M||_F^2 is rounding noise
-  const double tiny = fro * 2.0e-29;
+  // columns whose norm^2 is below noise_rel ||M||_F^2 do not count for convergence
+  const double tiny = fro * noise_rel;
   int sw = jacobi_core(m, n, W, Vw, max_sweeps, tol, tiny, &flag);
   __syncthreads();
   double* Sb = S + (long long)b * n;
@@ -176,7 +176,7 @@ constexpr int kCoopThreads = 256;
 __global__ void __launch_bounds__(kCoopThreads)
 svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* __restrict__ U,
                 double* __restrict__ S, double* __restrict__ V, double* __restrict__ work, int* __restrict__ flags,
-                int* __restrict__ status, int max_sweeps, double tol) {
+                int* __restrict__ status, int max_sweeps, double tol, double noise_rel) {
   cg::grid_group grid = cg::this_grid();
   const long long mn = (long long)m * n, nn = (long long)n * n;
   const int lane = threadIdx.x & 31;
@@ -205,7 +205,7 @@ svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* _
     if (lane == 0) atomicAdd(&tinyv[b], a);
   }
   grid.sync();
-  if (gthread < batch) tinyv[gthread] *= 2.0e-29;   // (64 eps)^2 ||M||_F^2
+  if (gthread < batch) tinyv[gthread] *= noise_rel;   // see svd_kernel
   grid.sync();
   const int np = n + (n & 1);
   const long long per = np / 2;
@@ -310,7 +310,7 @@ svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* _
 static bool fits_smem(int m, int n) { return (long long)(m + n) * n * 8 <= 40 * 1024; }
 
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V, double* work,
-                int* status, cudaStream_t s) {
+                int* status, cudaStream_t s, double noise_rel) {
   if (batch == 0 || n == 0) return;
   SCTM_CHECK(m >= n, "svd expects rows >= columns");
   const int max_sweeps = 60;
@@ -335,14 +335,14 @@ void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, 
     ProfScope ps(PF_SVD, s, (double)batch * 8.0 * 0.5 * n * (n - 1) * (12.0 * m + 6.0 * n),
                  (double)batch * 8.0 * (2.0 * m * n + 2.0 * n * n + n));
     void* args[] = {(void*)&m, (void*)&n, (void*)&batch, (void*)&M, (void*)&U, (void*)&S, (void*)&V,
-                    (void*)&work, (void*)&flags, (void*)&status, (void*)&max_sweeps, (void*)&tol};
+                    (void*)&work, (void*)&flags, (void*)&status, (void*)&max_sweeps, (void*)&tol, (void*)&noise_rel};
     SCTM_CUDA(cudaLaunchCooperativeKernel((void*)svd_coop_kernel, dim3(grid), dim3(kCoopThreads), args, 0, s));
     return;
   }
   // flops: one-sided Jacobi ~ 8 sweeps x n(n-1)/2 pairs x (6m + 6m + 6n) (estimate)
   ProfScope ps(PF_SVD, s, (double)batch * 8.0 * 0.5 * n * (n - 1) * (12.0 * m + 6.0 * n),
                (double)batch * 8.0 * (2.0 * m * n + 2.0 * n * n + n));
-  svd_kernel<<<batch, kSvdThreads, smem, s>>>(m, n, M, U, S, V, work, status, max_sweeps, tol, in_smem);
+  svd_kernel<<<batch, kSvdThreads, smem, s>>>(m, n, M, U, S, V, work, status, max_sweeps, tol, noise_rel, in_smem);
   SCTM_CUDA(cudaGetLastError());
 }
 

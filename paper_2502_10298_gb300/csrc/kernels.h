@@ -22,8 +22,11 @@ void launch_gaussian(long long rows, long long cols, unsigned long long seed, do
 
 // Batched SVD of m x n row-major matrices (m >= n): M = U diag(S) V^T with
 // U m x n, V n x n, S descending.
+// noise_rel > 0: a column pair in which either column has norm^2 below
+// noise_rel ||M||_F^2 still rotates but never keeps the sweep loop going (for
+// decompositions whose noise-level directions are discarded afterwards).
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V,
-                double* work, int* status, cudaStream_t s);
+                double* work, int* status, cudaStream_t s, double noise_rel = 0.0);
 size_t svd_work_doubles(int m, int n, int batch);
 
 // out[g] = alpha * in[g] + beta * out[g] over one index group g (strides sa = in, sc = out).
@@ -70,6 +73,19 @@ void launch_dot(int batch, long long n, const double* x, const double* y, long l
                 double* out, double* partial, cudaStream_t s);
 
 void launch_fill(long long n, double v, double* x, cudaStream_t s);
+
+// Column-wise conjugate gradient on rows x r blocks (row-major), one system per
+// column: update Y += a P, R -= a Q with a_j = rr_j / pq_j (0 if either is not
+// positive); direction P = R + b P with b_j = rr_new_j / rr_j.
+void launch_cg_update(long long rows, int r, const double* P, const double* Q, double* Y, double* R,
+                      const double* rr, const double* pq, cudaStream_t s);
+void launch_cg_direction(long long rows, int r, double* P, const double* R, const double* rr_new, const double* rr,
+                         cudaStream_t s);
+
+// Batched Cholesky QR factor: G (batch of r x r Gram matrices, overwritten) ->
+// T = R^+ with G = R^T R; pivots below tol_rel * max diag deflated (zero row of
+// R, zero column of T).
+void launch_chol_qr_factor(int r, int batch, double* G, double* T, double tol_rel, cudaStream_t s);
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s);
 
 }  // namespace sctm

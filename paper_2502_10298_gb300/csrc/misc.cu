@@ -75,6 +75,7 @@ __global__ void spectrum_map_kernel(int batch, int n, int kout, const double* S,
 void launch_spectrum_map(int batch, int n, int kout, const double* S, double* w, double cutoff, int mode,
                          cudaStream_t s) {
   if (batch * kout == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   spectrum_map_kernel<<<grid_for(batch * kout), kThreads, 0, s>>>(batch, n, kout, S, w, cutoff, mode);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -103,6 +104,7 @@ void launch_sign_find(int rows, int cols, const double* P, long long rs, long lo
                       cudaStream_t s) {
   if (rows == 0) return;
   long long threads = (long long)rows * 32;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   sign_find_kernel<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, s>>>(rows, cols, P, rs, cs, sgn);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -151,6 +153,7 @@ __global__ void spectrum_adj_kernel(int n, int kout, const double* S, const doub
 void launch_spectrum_adj(int n, int kout, const double* S, const double* wbar, double* Sbar, double cutoff,
                          int mode, cudaStream_t s) {
   if (kout == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   spectrum_adj_kernel<<<(kout + 255) / 256, 256, 0, s>>>(n, kout, S, wbar, Sbar, cutoff, mode);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -170,6 +173,7 @@ __global__ void rescale_adj_kernel(long long n, const double* ybar, const double
 void launch_rescale_adj(long long n, const double* ybar, const double* y, const double* m, const long long* k,
                         const double* xk_sign, const double* dot, double* xbar, cudaStream_t s) {
   if (n == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   rescale_adj_kernel<<<grid_for(n), kThreads, 0, s>>>(n, ybar, y, m, k, xk_sign, dot, xbar);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -231,7 +235,7 @@ __global__ void maxabs_final_scale_kernel(long long n, double* X, long long stri
 void launch_rescale(int batch, long long n, double* X, long long stride, double* scale, long long* argmax,
                     double* partial, cudaStream_t s) {
   if (batch == 0 || n == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 2);
   maxabs_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, X, stride, partial);
   SCTM_CUDA(cudaGetLastError());
   maxabs_final_scale_kernel<<<batch, 1024, 0, s>>>(n, X, stride, partial, scale, argmax);
@@ -264,7 +268,7 @@ __global__ void dot_final_kernel(int batch, const double* partial, double* out) 
 void launch_dot(int batch, long long n, const double* x, const double* y, long long stride, double* out,
                 double* partial, cudaStream_t s) {
   if (batch == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 2);
   dot_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, x, y, stride, partial);
   SCTM_CUDA(cudaGetLastError());
   dot_final_kernel<<<(batch + 127) / 128, 128, 0, s>>>(batch, partial, out);
@@ -281,11 +285,13 @@ __global__ void axpy_kernel(long long n, double a, const double* x, double* y) {
 }
 void launch_fill(long long n, double v, double* x, cudaStream_t s) {
   if (n == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   fill_kernel<<<grid_for(n), kThreads, 0, s>>>(n, v, x);
   SCTM_CUDA(cudaGetLastError());
 }
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s) {
   if (n == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -310,7 +316,51 @@ __global__ void gaussian_kernel(long long n, unsigned long long seed, double* X)
 void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s) {
   long long n = rows * cols;
   if (n == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   gaussian_kernel<<<grid_for(n), kThreads, 0, s>>>(n, seed, X);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- column CG
+// Conjugate-gradient steps for r independent shifted systems stored as the
+// columns of rows x r row-major blocks (one scalar per column).
+__global__ void cg_update_kernel(long long rows, int r, const double* __restrict__ P, const double* __restrict__ Q,
+                                 double* __restrict__ Y, double* __restrict__ R, const double* __restrict__ rr,
+                                 const double* __restrict__ pq) {
+  const long long total = rows * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % r);
+    const double a = (rr[j] > 0.0 && pq[j] > 0.0) ? rr[j] / pq[j] : 0.0;
+    Y[e] = fma(a, P[e], Y[e]);
+    R[e] = fma(-a, Q[e], R[e]);
+  }
+}
+
+__global__ void cg_direction_kernel(long long rows, int r, double* __restrict__ P, const double* __restrict__ R,
+                                    const double* __restrict__ rr_new, const double* __restrict__ rr) {
+  const long long total = rows * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % r);
+    const double b = rr[j] > 0.0 ? rr_new[j] / rr[j] : 0.0;
+    P[e] = fma(b, P[e], R[e]);
+  }
+}
+
+void launch_cg_update(long long rows, int r, const double* P, const double* Q, double* Y, double* R,
+                      const double* rr, const double* pq, cudaStream_t s) {
+  if (rows * r == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  cg_update_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, Q, Y, R, rr, pq);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+void launch_cg_direction(long long rows, int r, double* P, const double* R, const double* rr_new, const double* rr,
+                         cudaStream_t s) {
+  if (rows * r == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  cg_direction_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, R, rr_new, rr);
   SCTM_CUDA(cudaGetLastError());
 }
 

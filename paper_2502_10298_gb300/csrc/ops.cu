@@ -245,31 +245,13 @@ Tensor copy(Ctx& c, const Tensor& X) {
 }
 
 // ------------------------------------------------------------------ svd
-SVDResult svd(Ctx& c, const Tensor& M_in, double eps_l) {
-  SCTM_CHECK(M_in.nd == 2 && M_in.shape[0] >= M_in.shape[1], "svd expects a matrix with rows >= columns");
-  const int m = M_in.shape[0], n = M_in.shape[1];
-  bool tap = c.tape.active;
-  Tensor M = M_in;
-  if (!M.contiguous()) {
-    c.tape.active = false;  // the copy's adjoint is added explicitly below
-    M = copy(c, M_in);
-    c.tape.active = tap;
-  }
-  SVDResult r;
-  r.U = c.empty({m, n});
-  r.S = c.empty({n});
-  r.V = c.empty({n, n});
-  size_t mk = c.arena.mark();
-  double* work = nullptr;
-  size_t wn = svd_work_doubles(m, n, 1);
-  if (wn) work = c.arena.alloc((long long)wn);
-  launch_svd(m, n, 1, M.data, r.U.data, r.S.data, r.V.data, work, c.svd_status, c.stream);
-  if (!tap) c.arena.release(mk);  // later work is stream-ordered after the kernel
-  if (!tap || !M_in.grad) return r;
-  Tensor U = r.U, S = r.S, V = r.V, Min = M_in;
-  // M_bar = U [ F o (J - J^T) S + diag(S_bar) + S F o (K - K^T) ] V^T,
-  // J = U^T U_bar, K = V^T V_bar.  For m > n the projector code uses only S and V
-  // (U_bar = 0), so the (1 - U U^T) U_bar S^-1 V^T term of the thin SVD vanishes.
+// Reverse pass of M = U S V^T (square or tall):
+// M_bar = U [ F o (J - J^T) S + diag(S_bar) + S F o (K - K^T) ] V^T,
+// J = U^T U_bar, K = V^T V_bar.  For m > n the projector code uses only S and V
+// (U_bar = 0), so the (1 - U U^T) U_bar S^-1 V^T term of the thin SVD vanishes.
+static void record_svd_adjoint(Ctx& c, const SVDResult& r, const Tensor& Min, double eps_l) {
+  const int m = r.U.shape[0], n = r.U.shape[1];
+  Tensor U = r.U, S = r.S, V = r.V;
   c.tape.push([&c, U, S, V, Min, m, n, eps_l]() {
     bool t = c.tape.active;
     c.tape.active = false;
@@ -283,7 +265,41 @@ SVDResult svd(Ctx& c, const Tensor& M_in, double eps_l) {
     einsum_into(c, "aj,bj->ab", T1, V, grad_view(Min), 1.0, 1.0, false);
     c.tape.active = t;
   });
-  return r;
+}
+
+SVDResult svd(Ctx& c, const Tensor& M_in, double eps_l) { return svd_many(c, {M_in}, eps_l)[0]; }
+
+std::vector<SVDResult> svd_many(Ctx& c, const std::vector<Tensor>& Ms, double eps_l) {
+  const int nb = (int)Ms.size();
+  std::vector<SVDResult> out(nb);
+  if (nb == 0) return out;
+  const int m = Ms[0].shape[0], n = Ms[0].shape[1];
+  for (const Tensor& M : Ms)
+    SCTM_CHECK(M.nd == 2 && M.shape[0] == m && M.shape[1] == n && m >= n,
+               "svd expects equally shaped matrices with rows >= columns");
+  bool tap = c.tape.active;
+  // one contiguous batch (a view of the input when there is a single contiguous matrix)
+  Tensor Mb;
+  if (nb == 1 && Ms[0].contiguous()) {
+    Mb = Ms[0];
+  } else {
+    c.tape.active = false;   // the inputs' adjoints are added explicitly below
+    Mb = c.empty({nb, m, n});
+    for (int i = 0; i < nb; ++i) copy_into(c, Ms[i], Mb.sub(0, i));
+    c.tape.active = tap;
+  }
+  Tensor Ub = c.empty({nb, m, n}), Sb = c.empty({nb, n}), Vb = c.empty({nb, n, n});
+  size_t mk = c.arena.mark();
+  double* work = nullptr;
+  size_t wn = svd_work_doubles(m, n, nb);
+  if (wn) work = c.arena.alloc((long long)wn);
+  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream);
+  if (!tap) c.arena.release(mk);  // later work is stream-ordered after the kernel
+  for (int i = 0; i < nb; ++i) {
+    out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};
+    if (tap && Ms[i].grad) record_svd_adjoint(c, out[i], Ms[i], eps_l);
+  }
+  return out;
 }
 
 // ------------------------------------------------------------------ spectrum

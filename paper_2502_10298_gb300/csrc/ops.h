@@ -42,6 +42,8 @@ struct SVDResult {
   Tensor U, S, V;
 };
 SVDResult svd(Ctx& c, const Tensor& M, double eps_l);
+// SVDs of equally shaped matrices in one launch, each with its own adjoint
+std::vector<SVDResult> svd_many(Ctx& c, const std::vector<Tensor>& Ms, double eps_l);
 
 // w[k] = f(S[k]) for k < kout with a cutoff relative to S[0] (see kernels.h modes)
 Tensor spectrum_map(Ctx& c, const Tensor& S, int kout, double cutoff, int mode);

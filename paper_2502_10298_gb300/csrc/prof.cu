@@ -12,6 +12,7 @@ struct Rec {
   cudaEvent_t a, b;
   int fam;
   double flops, bytes;
+  int launches;
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
@@ -38,7 +39,7 @@ void prof_enable(bool on) {
 
 bool prof_enabled() { return g_on; }
 
-ProfScope::ProfScope(int family, cudaStream_t s, double flops, double bytes) : fam(family), st(s) {
+ProfScope::ProfScope(int family, cudaStream_t s, double flops, double bytes, int launches) : fam(family), st(s) {
   if (!g_on) return;
   std::lock_guard<std::mutex> l(g_mu);
   Rec r;
@@ -47,6 +48,7 @@ ProfScope::ProfScope(int family, cudaStream_t s, double flops, double bytes) : f
   r.fam = family;
   r.flops = flops;
   r.bytes = bytes;
+  r.launches = launches;
   SCTM_CUDA(cudaEventRecord(r.a, s));
   slot = (int)g_recs.size();
   g_recs.push_back(r);
@@ -66,7 +68,7 @@ void prof_collect(double* out) {
     float ms = 0;
     SCTM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
     out[r.fam * 4 + 0] += ms;
-    out[r.fam * 4 + 1] += 1;
+    out[r.fam * 4 + 1] += r.launches;
     out[r.fam * 4 + 2] += r.flops;
     out[r.fam * 4 + 3] += r.bytes;
   }

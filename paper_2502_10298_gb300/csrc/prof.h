@@ -7,7 +7,7 @@
 
 namespace sctm {
 
-enum ProfFamily { PF_CONTRACT = 0, PF_SVD = 1, PF_MISC = 2, PF_N = 3 };
+enum ProfFamily { PF_CONTRACT = 0, PF_SVD = 1, PF_MISC = 2, PF_TENSOR = 3, PF_N = 4 };
 
 void prof_enable(bool on);
 bool prof_enabled();
@@ -15,7 +15,8 @@ bool prof_enabled();
 void prof_collect(double* out);
 
 struct ProfScope {
-  ProfScope(int family, cudaStream_t s, double flops, double bytes);
+  // launches: kernel launches inside the scope
+  ProfScope(int family, cudaStream_t s, double flops, double bytes, int launches = 1);
   ~ProfScope();
   int fam;
   cudaStream_t st;

@@ -417,8 +417,6 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
   float* pb = scratch + 2 * d.B * Mp * Kp;
   SCTM_CHECK((reinterpret_cast<uintptr_t>(pa) & 127) == 0 && (reinterpret_cast<uintptr_t>(pb) & 127) == 0,
              "tensor-core scratch misaligned");
-  ProfScope ps(PF_CONTRACT, s, 2.0 * d.B * d.M * d.N * d.K,
-               8.0 * d.B * (d.M * d.K + d.K * d.N + d.M * d.N * (d.beta != 0 ? 2 : 1)));
   // operand A: rows = m, strides .sa ; operand B: rows = n, strides .sb
   PackDesc pA;
   pA.bat = d.bat, pA.rows = d.m, pA.k = d.k;
@@ -431,10 +429,17 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
     pB.k.sa[i] = d.k.sb[i];
   }
   pB.nb = d.B, pB.R = d.N, pB.K = d.K, pB.Rp = Np, pB.Kp = Kp, pB.k_inner = d.b_n_inner ? 0 : 1;
-  pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pA, A, pa);
-  SCTM_CUDA(cudaGetLastError());
-  pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pB, B, pb);
-  SCTM_CUDA(cudaGetLastError());
+  // packing is a gather: reads the FP64 operand once, writes its hi and lo panels
+  {
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.M * d.K + 8.0 * d.B * Kp * Mp);
+    pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pA, A, pa);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  {
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.N * d.K + 8.0 * d.B * Kp * Np);
+    pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pB, B, pb);
+    SCTM_CUDA(cudaGetLastError());
+  }
   CUtensorMap mA = panel_map(pa, d.B, Mp, Kp, TC_BM);
   CUtensorMap mB = panel_map(pb, d.B, Np, Kp, TC_BN);
   TcEpi e;
@@ -447,6 +452,10 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
     attr = true;
   }
   dim3 grid((unsigned)((long long)e.num_m * e.num_n), (unsigned)d.B);
+  // algorithmic work 2 B M N K (the tensor pipe executes three TF32 products
+  // per multiply-add); bytes: the hi/lo panels read once, the FP64 result written
+  ProfScope ps(PF_TENSOR, s, 2.0 * d.B * d.M * d.N * d.K,
+               8.0 * d.B * Kp * (Mp + Np) + 8.0 * d.B * d.M * d.N * (d.beta != 0 ? 2 : 1));
   tc_gemm_kernel<<<grid, TC_THREADS_V2, TC_SMEM, s>>>(mA, mB, e, (int)(Kp / TC_BK), C, status);
   SCTM_CUDA(cudaGetLastError());
 }

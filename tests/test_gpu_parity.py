@@ -156,14 +156,17 @@ def test_jacobi_svd_against_lapack(S, m, n):
     assert np.abs(U.T @ U - np.eye(n)).max() < 1e-11
 
 
+@pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("Lx,Ly,D,chi", [(1, 1, 3, 9), (2, 2, 3, 9)])
-def test_mixed_mode_energy_and_gradient(S, Lx, Ly, D, chi):
-    """precision=1 (FP32 contractions, randomized projectors where alpha > 2 chi):
-    energy within 1e-6 per site and gradient within 1e-4 (norm) of the FP64 oracle."""
+def test_mixed_mode_energy_and_gradient(S, Lx, Ly, D, chi, prec):
+    """precision 1 (large contractions on the tensor cores) and 2 (FP32 on the
+    CUDA cores); randomized projectors forced on (randomized_min=1, alpha > 2 chi
+    here): energy within 1e-6 per site and gradient within 1e-4 (norm) of the
+    FP64 oracle."""
     A = _near(Lx, Ly, D, 0.3, seed=21)
     h, hd = (HR, None) if Lx == 1 else (H, 0.5 * H)
     sweeps = 2
-    with S.SplitCTMRG(Lx, Ly, 2, D, chi, precision=1) as s:
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, precision=prec, randomized_min=1) as s:
         e, g = s.energy_grad(torch.tensor(A, device="cuda"), sweeps, h, hd)
     Ao = torch.tensor(A).requires_grad_(True)
     Ac = [[Ao[x, y] for y in range(Ly)] for x in range(Lx)]
@@ -171,4 +174,21 @@ def test_mixed_mode_energy_and_gradient(S, Lx, Ly, D, chi):
     eo.backward()
     assert abs(e - float(eo)) < 1e-6
     rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
+    assert rel < 1e-4, rel
+
+
+def test_mixed_randomized_matches_fp64_gpu(S):
+    """Randomized projectors at a size where they are the default (the truncated
+    spaces chi D = 256 and chi p D = 512 exceed 2 chi): mixed energy within 1e-6
+    per site and gradient within 1e-4 of the FP64 GPU path (exact Jacobi SVDs),
+    both with the mixed mode's singular-value cutoff 1e-6."""
+    D, chi, sweeps = 4, 64, 2
+    A = _near(1, 1, D, 0.3, seed=5)
+    At = torch.tensor(A, device="cuda")
+    with S.SplitCTMRG(1, 1, 2, D, chi, precision=0, svd_cutoff=1e-6) as s:
+        e0, g0 = s.energy_grad(At, sweeps, HR, None)
+    with S.SplitCTMRG(1, 1, 2, D, chi, precision=1) as s:
+        e1, g1 = s.energy_grad(At, sweeps, HR, None)
+    assert abs(e1 - e0) < 1e-6, (e0, e1)
+    rel = float((g1 - g0).norm() / g0.norm())
     assert rel < 1e-4, rel
