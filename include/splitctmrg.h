@@ -113,8 +113,9 @@ SCTM_API int energy_2x2(sctm_handle h, const double* h_nn_host, const double* h_
 
 /* Energy and its gradient with respect to A_cell: initial environment,
  * `sweeps` full steps, 2x2 energy, then the reverse pass through all of it
- * (per-sweep checkpoints, hand-written adjoints, SVD adjoint with Lorentzian
- * broadening).  grad_dev has the layout of A_cell.  Leaves the converged
+ * (one environment checkpoint per directional move, each move recomputed with
+ * hand-written adjoints; SVD adjoint with Lorentzian broadening; the energy is
+ * differentiated one 2x2 patch at a time).  grad_dev has the layout of A_cell.  Leaves the converged
  * environment in the handle. */
 SCTM_API int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const double* h_nn_host,
                 const double* h_diag_host, double* e_per_site, double* grad_dev);

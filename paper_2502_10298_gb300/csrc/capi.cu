@@ -394,40 +394,40 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
     SCTM_CUDA(cudaMemcpyAsync(h->A, A_cell_dev, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     SCTM_CUDA(cudaMemsetAsync(h->Agrad, 0, nA * sizeof(double), c.stream));
     size_t base = c.arena.mark();
-    // checkpoints of the environment at the start of every sweep (+ final)
-    double* ck = c.arena.alloc(nE * (sweeps + 1));
+    // checkpoints of the environment before every directional move (+ final):
+    // the reverse pass recomputes one move at a time, taped
+    const int nmoves = 4 * sweeps;
+    double* ck = c.arena.alloc(nE * (nmoves + 1));
     double* gbuf = c.arena.alloc(nE);
     size_t top = c.arena.mark();
-    // forward: init + sweeps, untaped
+    // forward: init + moves, untaped
     c.tape.active = false;
     bind_A(h, false);
     init_env(c, P, h->cell);
     save_env(h, ck);
     bind_store(h, ck);
     c.arena.release(top);
-    for (int s = 0; s < sweeps; ++s) {
-      for (int d = 0; d < 4; ++d) {
-        move(c, P, h->cell, d);
-        save_env(h, ck + (s + 1) * nE);   // in-sweep moves write into the next checkpoint
-        bind_store(h, ck + (s + 1) * nE);
-        c.arena.release(top);
-      }
+    for (int mv = 0; mv < nmoves; ++mv) {
+      move(c, P, h->cell, mv % 4);
+      save_env(h, ck + (mv + 1) * nE);
+      bind_store(h, ck + (mv + 1) * nE);
+      c.arena.release(top);
     }
     check_svd(h);
-    // energy on the final environment, taped
+    // energy on the final environment, taped patch by patch
     bind_A(h, true);
     c.tape.active = true;
-    bind_leaves(h, ck + sweeps * nE);
+    bind_leaves(h, ck + nmoves * nE);
     *e_per_site = energy_value(h, h_nn_host, h_diag_host, true);
     read_env_grad(h, gbuf);
     c.tape.active = false;
     c.arena.release(top);
-    // reverse through the sweeps, one checkpointed sweep at a time
-    for (int s = sweeps - 1; s >= 0; --s) {
+    // reverse through the moves, one checkpointed move at a time
+    for (int mv = nmoves - 1; mv >= 0; --mv) {
       c.tape.active = true;
-      bind_leaves(h, ck + s * nE);
+      bind_leaves(h, ck + mv * nE);
       std::vector<SiteEnv> leaves = h->cell.env;
-      for (int d = 0; d < 4; ++d) move(c, P, h->cell, d);
+      move(c, P, h->cell, mv % 4);
       seed_env_grad(h, gbuf);
       c.tape.backward();
       h->cell.env = leaves;
@@ -445,7 +445,7 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
     SCTM_CUDA(cudaMemcpyAsync(grad_dev, h->Agrad, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     // leave the converged environment in the store
     bind_A(h, false);
-    bind_store(h, ck + sweeps * nE);
+    bind_store(h, ck + nmoves * nE);
     save_env(h, h->store);
     bind_store(h, h->store);
     SCTM_CUDA(cudaStreamSynchronize(c.stream));

@@ -129,17 +129,24 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
 // Reverse pass of a truncated SVD (U_r, S_r, V_r) of M = rhoB rhoT (beta x
 // beta, never formed).  Pairs inside the r computed triplets use the usual
 // broadened coefficients; the coupling of triplet i to the unknown rest of the
-// spectrum is exact: with P = 1 - U U^T, Q = 1 - V V^T, the columns
+// spectrum follows first-order perturbation theory summed over it: with
+// P = 1 - U U^T, Q = 1 - V V^T the columns
 //   y_i = (s_i^2 - P M M^T P)^-1 P (s_i u_bar_i + M v_bar_i),
 //   z_i = (s_i^2 - Q M^T M Q)^-1 Q (M^T u_bar_i + s_i v_bar_i)
-// (first-order perturbation theory summed over the complement) are found by
-// column-wise conjugate gradients, which only apply M and M^T.  Then
+// are found by column-wise conjugate gradients, which only apply M and M^T.
+// Then
 //   M_bar = U X V^T + Y V^T + U Z^T,
 //   X = F o (J - J^T) S + diag(S_bar) + S F o (K - K^T), J = U^T U_bar, K = V^T V_bar,
 // applied without forming M_bar:  rhoB_bar += M_bar rhoT^T, rhoT_bar += rhoB^T M_bar.
-// The systems are positive definite for the kept triplets (s_i > s_{r+1});
-// columns without cotangent stay zero.
+// The systems are positive definite when s_i > s_{r+1}, but the products with
+// M carry the rounding of the contraction arithmetic (about 1e-7 s_1^2 in
+// mixed mode), and the randomized basis leaks a little of the top spectrum
+// into P M M^T P; so the solve is used for s_i >= 1e-3 s_1 only and a column's
+// iteration stops where its operator is not safely positive definite (see
+// launch_cg_update); smaller kept values take the leading term
+// y_i = P u_bar_i / s_i, z_i = Q v_bar_i / s_i.  Columns without cotangent stay zero.
 static constexpr int kComplementCG = 10;
+static constexpr double kComplementMinRel = 1e-3;
 
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l) {
@@ -162,20 +169,30 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
   };
   Tensor s2 = c.empty({k});
   einsum_into(c, "j,j->j", S, S, s2, 1.0, 0.0, false);   // s_j^2
+  // masks: m_j = 1 for s_j >= kComplementMinRel s_1 (solved), else 0 (leading term)
+  Tensor msk = spectrum_map(c, S, k, kComplementMinRel, 2);
+  Tensor nmsk = c.empty({k});
+  launch_fill(k, 1.0, nmsk.data, c.stream);
+  launch_axpy(k, -1.0, msk.data, nmsk.data, c.stream);
+  Tensor sinv = spectrum_map(c, S, k, 1e-14, 0);              // s^-1/2
   // column-wise CG for (diag(s^2) - B) Y = rhs, B = P op P
   auto solve = [&](const Tensor& Bas, Tensor rhs, bool left) {
     Tensor Yv = c.zeros({nb, k});
     Tensor R = copy(c, rhs);
     Tensor Pd = copy(c, rhs);
-    Tensor rr = einsum(c, "aj,aj->j", R, R), rr2 = c.empty({k});
+    Tensor rr = c.empty({k}), rr2 = c.empty({k}), pq = c.empty({k}), pp = c.empty({k});
+    int* frozen = reinterpret_cast<int*>(c.zeros({(k + 1) / 2}).data);
+    launch_coldot(nb, k, R.data, R.data, rr.data, c.stream);
     for (int it = 0; it < kComplementCG; ++it) {
       Tensor Bp = project(Bas, left ? Mx(MTx(Pd)) : MTx(Mx(Pd)));
       Tensor Q = scale_dim(c, Pd, 1, s2);
       launch_axpy(Q.numel(), -1.0, Bp.data, Q.data, c.stream);          // Q = s^2 p - B p
-      Tensor pq = einsum(c, "aj,aj->j", Pd, Q);
-      launch_cg_update(nb, k, Pd.data, Q.data, Yv.data, R.data, rr.data, pq.data, c.stream);
-      einsum_into(c, "aj,aj->j", R, R, rr2, 1.0, 0.0, false);
-      launch_cg_direction(nb, k, Pd.data, R.data, rr2.data, rr.data, c.stream);
+      launch_coldot(nb, k, Pd.data, Q.data, pq.data, c.stream);
+      launch_coldot(nb, k, Pd.data, Pd.data, pp.data, c.stream);
+      launch_cg_update(nb, k, Pd.data, Q.data, Yv.data, R.data, rr.data, pq.data, pp.data, s2.data, frozen,
+                       c.stream);
+      launch_coldot(nb, k, R.data, R.data, rr2.data, c.stream);
+      launch_cg_direction(nb, k, Pd.data, R.data, rr2.data, rr.data, frozen, c.stream);
       std::swap(rr, rr2);
     }
     return Yv;
@@ -187,8 +204,18 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
   Tensor bZ = scale_dim(c, gV, 1, S);
   launch_axpy(bZ.numel(), 1.0, MTx(gU).data, bZ.data, c.stream);
   bZ = project(V, bZ);
-  Tensor A = solve(U, bY, true);
-  Tensor Bm = solve(V, bZ, false);
+  Tensor A = solve(U, scale_dim(c, bY, 1, msk), true);
+  Tensor Bm = solve(V, scale_dim(c, bZ, 1, msk), false);
+  // leading terms for the unmasked columns: P U_bar S^-1, Q V_bar S^-1
+  {
+    Tensor w = c.empty({k});
+    einsum_into(c, "j,j->j", sinv, sinv, w, 1.0, 0.0, false);   // 1/s
+    einsum_into(c, "j,j->j", w, nmsk, w, 1.0, 0.0, false);
+    Tensor yl = project(U, scale_dim(c, gU, 1, w));
+    Tensor zl = project(V, scale_dim(c, gV, 1, w));
+    launch_axpy(A.numel(), 1.0, yl.data, A.data, c.stream);
+    launch_axpy(Bm.numel(), 1.0, zl.data, Bm.data, c.stream);
+  }
   // L1 = U X + Y
   Tensor L1 = c.empty({nb, k});
   einsum_into(c, "ai,ij->aj", U, X, L1, 1.0, 0.0, false);

@@ -74,13 +74,17 @@ void launch_dot(int batch, long long n, const double* x, const double* y, long l
 
 void launch_fill(long long n, double v, double* x, cudaStream_t s);
 
-// Column-wise conjugate gradient on rows x r blocks (row-major), one system per
-// column: update Y += a P, R -= a Q with a_j = rr_j / pq_j (0 if either is not
-// positive); direction P = R + b P with b_j = rr_new_j / rr_j.
+// Column-wise conjugate gradient on rows x r blocks (row-major), one shifted
+// system (s_j^2 - B) y_j = b_j per column: update Y += a P, R -= a Q with
+// a_j = rr_j / pq_j; a column freezes (a = 0 from then on, direction kept) once
+// pq_j <= 0.1 s2_j pp_j or rr_j <= 0.  Direction P = R + (rr_new_j / rr_j) P.
 void launch_cg_update(long long rows, int r, const double* P, const double* Q, double* Y, double* R,
-                      const double* rr, const double* pq, cudaStream_t s);
+                      const double* rr, const double* pq, const double* pp, const double* s2, int* frozen,
+                      cudaStream_t s);
 void launch_cg_direction(long long rows, int r, double* P, const double* R, const double* rr_new, const double* rr,
-                         cudaStream_t s);
+                         const int* frozen, cudaStream_t s);
+// out[j] = sum_a X[a, j] Y[a, j] for rows x r row-major X, Y (FP64)
+void launch_coldot(long long rows, int r, const double* X, const double* Y, double* out, cudaStream_t s);
 
 // Batched Cholesky QR factor: G (batch of r x r Gram matrices, overwritten) ->
 // T = R^+ with G = R^T R; pivots below tol_rel * max diag deflated (zero row of

@@ -322,45 +322,84 @@ void launch_gaussian(long long rows, long long cols, unsigned long long seed, do
 }
 
 // ---------------------------------------------------------------- column CG
-// Conjugate-gradient steps for r independent shifted systems stored as the
-// columns of rows x r row-major blocks (one scalar per column).
+// Conjugate-gradient steps for r independent shifted systems (s_j^2 - B) y_j =
+// b_j stored as the columns of rows x r row-major blocks (one scalar per column).
+// A column is frozen (its step set to zero from then on) as soon as the
+// Rayleigh quotient pq / pp of its search direction drops below 0.1 s_j^2:
+// the operator is then not safely positive definite along it and further
+// steps would amplify rounding instead of converging.
+
+// out[j] = sum_a X[a, j] Y[a, j] (FP64), X, Y rows x r row-major
+__global__ void coldot_kernel(long long rows, int r, const double* __restrict__ X, const double* __restrict__ Y,
+                              double* __restrict__ out) {
+  __shared__ double part[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j = blockIdx.x * 32 + tx;
+  double acc = 0.0;
+  if (j < r)
+    for (long long a = ty; a < rows; a += 8) acc = fma(X[a * r + j], Y[a * r + j], acc);
+  part[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && j < r) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += part[i][tx];
+    out[j] = t;
+  }
+}
+
+void launch_coldot(long long rows, int r, const double* X, const double* Y, double* out, cudaStream_t s) {
+  if (r == 0) return;
+  ProfScope ps_(PF_MISC, s, 2.0 * rows * r, 16.0 * rows * r);
+  coldot_kernel<<<(r + 31) / 32, dim3(32, 8), 0, s>>>(rows, r, X, Y, out);
+  SCTM_CUDA(cudaGetLastError());
+}
+
 __global__ void cg_update_kernel(long long rows, int r, const double* __restrict__ P, const double* __restrict__ Q,
                                  double* __restrict__ Y, double* __restrict__ R, const double* __restrict__ rr,
-                                 const double* __restrict__ pq) {
+                                 const double* __restrict__ pq, const double* __restrict__ pp,
+                                 const double* __restrict__ s2, int* __restrict__ frozen) {
   const long long total = rows * r;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e % r);
-    const double a = (rr[j] > 0.0 && pq[j] > 0.0) ? rr[j] / pq[j] : 0.0;
+    const bool ok = !frozen[j] && rr[j] > 0.0 && pq[j] > 0.1 * s2[j] * pp[j];
+    if (!ok) {
+      if (e < r) frozen[j] = 1;   // one writer per column (the row-0 thread)
+      continue;
+    }
+    const double a = rr[j] / pq[j];
     Y[e] = fma(a, P[e], Y[e]);
     R[e] = fma(-a, Q[e], R[e]);
   }
 }
 
 __global__ void cg_direction_kernel(long long rows, int r, double* __restrict__ P, const double* __restrict__ R,
-                                    const double* __restrict__ rr_new, const double* __restrict__ rr) {
+                                    const double* __restrict__ rr_new, const double* __restrict__ rr,
+                                    const int* __restrict__ frozen) {
   const long long total = rows * r;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e % r);
+    if (frozen[j]) continue;
     const double b = rr[j] > 0.0 ? rr_new[j] / rr[j] : 0.0;
     P[e] = fma(b, P[e], R[e]);
   }
 }
 
 void launch_cg_update(long long rows, int r, const double* P, const double* Q, double* Y, double* R,
-                      const double* rr, const double* pq, cudaStream_t s) {
+                      const double* rr, const double* pq, const double* pp, const double* s2, int* frozen,
+                      cudaStream_t s) {
   if (rows * r == 0) return;
   ProfScope ps_(PF_MISC, s, 0.0, 0.0);
-  cg_update_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, Q, Y, R, rr, pq);
+  cg_update_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, Q, Y, R, rr, pq, pp, s2, frozen);
   SCTM_CUDA(cudaGetLastError());
 }
 
 void launch_cg_direction(long long rows, int r, double* P, const double* R, const double* rr_new, const double* rr,
-                         cudaStream_t s) {
+                         const int* frozen, cudaStream_t s) {
   if (rows * r == 0) return;
   ProfScope ps_(PF_MISC, s, 0.0, 0.0);
-  cg_direction_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, R, rr_new, rr);
+  cg_direction_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, R, rr_new, rr, frozen);
   SCTM_CUDA(cudaGetLastError());
 }
 

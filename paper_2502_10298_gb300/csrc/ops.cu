@@ -1,9 +1,11 @@
 // Differentiable device operations (see ops.h).
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 
 #include "ops.h"
+#include "prof.h"
 
 namespace sctm {
 
@@ -179,6 +181,12 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
   ContractDesc d = plan(sp, A, B, C);
   d.alpha = alpha;
   d.beta = beta;
+  if (prof_enabled()) {
+    char tag[160];
+    std::snprintf(tag, sizeof(tag), "%s B%lld M%lld N%lld K%lld%s", spec, d.B, d.M, d.N, d.K,
+                  c.fp32_compute ? "" : " f64");
+    prof_set_tag(tag);
+  }
   if (c.fp32_compute && c.tensor_cores && tc_eligible(d)) {
     size_t mk = c.arena.mark();
     float* scratch = reinterpret_cast<float*>(c.arena.alloc((long long)(tc_scratch_floats(d) + 1) / 2));
@@ -187,6 +195,7 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
   } else {
     launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute);
   }
+  if (prof_enabled()) prof_set_tag("");
   if (!record || !c.tape.active || !C.grad) return;
   std::string sa = sp.c + "," + sp.b + "->" + sp.a;
   std::string sb = sp.a + "," + sp.c + "->" + sp.b;

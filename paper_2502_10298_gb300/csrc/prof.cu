@@ -1,5 +1,10 @@
 // Per-kernel-family event timing (see prof.h).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.h"
@@ -13,12 +18,14 @@ struct Rec {
   int fam;
   double flops, bytes;
   int launches;
+  std::string tag;
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 size_t g_used = 0;
 bool g_on = false;
 std::mutex g_mu;
+thread_local std::string g_tag;
 
 cudaEvent_t take() {
   if (g_used < g_pool.size()) return g_pool[g_used++];
@@ -39,6 +46,10 @@ void prof_enable(bool on) {
 
 bool prof_enabled() { return g_on; }
 
+void prof_set_tag(const char* tag) {
+  if (g_on) g_tag = tag ? tag : "";
+}
+
 ProfScope::ProfScope(int family, cudaStream_t s, double flops, double bytes, int launches) : fam(family), st(s) {
   if (!g_on) return;
   std::lock_guard<std::mutex> l(g_mu);
@@ -49,6 +60,7 @@ ProfScope::ProfScope(int family, cudaStream_t s, double flops, double bytes, int
   r.flops = flops;
   r.bytes = bytes;
   r.launches = launches;
+  r.tag = g_tag;
   SCTM_CUDA(cudaEventRecord(r.a, s));
   slot = (int)g_recs.size();
   g_recs.push_back(r);
@@ -63,6 +75,8 @@ ProfScope::~ProfScope() {
 void prof_collect(double* out) {
   std::lock_guard<std::mutex> l(g_mu);
   for (int i = 0; i < PF_N * 4; ++i) out[i] = 0;
+  const bool tags = std::getenv("SCTM_PROFILE_TAGS") != nullptr;
+  std::map<std::string, std::pair<double, double>> by_tag;   // ms, flops
   for (auto& r : g_recs) {
     SCTM_CUDA(cudaEventSynchronize(r.b));
     float ms = 0;
@@ -71,6 +85,19 @@ void prof_collect(double* out) {
     out[r.fam * 4 + 1] += r.launches;
     out[r.fam * 4 + 2] += r.flops;
     out[r.fam * 4 + 3] += r.bytes;
+    if (tags) {
+      auto& t = by_tag[std::to_string(r.fam) + " " + r.tag];
+      t.first += ms;
+      t.second += r.flops;
+    }
+  }
+  if (tags) {
+    std::vector<std::pair<double, std::string>> v;
+    for (auto& kv : by_tag) v.push_back({kv.second.first, kv.first});
+    std::sort(v.rbegin(), v.rend());
+    for (size_t i = 0; i < v.size() && i < 40; ++i)
+      std::fprintf(stderr, "[prof] %9.2f ms %8.2f TF/s  %s\n", v[i].first,
+                   by_tag[v[i].second].second / (v[i].first * 1e-3 + 1e-30) / 1e12, v[i].second.c_str());
   }
   g_recs.clear();
   g_used = 0;

@@ -10,6 +10,10 @@ namespace sctm {
 enum ProfFamily { PF_CONTRACT = 0, PF_SVD = 1, PF_MISC = 2, PF_TENSOR = 3, PF_N = 4 };
 
 void prof_enable(bool on);
+// label attached to the scopes opened until the next call (e.g. an einsum
+// spec with its dimensions); with SCTM_PROFILE_TAGS set in the environment,
+// prof_collect also prints the 40 labels with the most device time to stderr
+void prof_set_tag(const char* tag);
 bool prof_enabled();
 // out: PF_N rows of {milliseconds, launches, flops, bytes}
 void prof_collect(double* out);
