@@ -74,6 +74,10 @@ typedef struct {
   int randomized_min;    /* mixed mode: randomized projectors only when the space
                             being truncated has at least this dimension (0: 256);
                             smaller ones use the exact FP64 decomposition        */
+  int adjoint_cg_steps;  /* mixed mode, reverse pass of randomized projectors: 0 =
+                            leading-order coupling to the unresolved spectrum;
+                            n > 0 = n conjugate-gradient steps on the first-order
+                            coupling (experimental)                                */
 } sctm_config;
 
 /* Create a handle.  stream: a cudaStream_t (NULL = legacy default stream). */

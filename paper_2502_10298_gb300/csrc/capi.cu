@@ -257,6 +257,8 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     SCTM_CHECK(cfg->power_steps >= 0 && cfg->power_steps <= 16, "power_steps must be in [0, 16]");
     if (cfg->power_steps > 0) P.power_steps = cfg->power_steps;
     if (cfg->randomized_min > 0) P.randomized_min = cfg->randomized_min;
+    SCTM_CHECK(cfg->adjoint_cg_steps >= 0 && cfg->adjoint_cg_steps <= 64, "adjoint_cg_steps must be in [0, 64]");
+    P.adjoint_cg_steps = cfg->adjoint_cg_steps;
     if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
     h->c.stream = (cudaStream_t)stream;
     const int chi = P.chi, D = P.D;

@@ -38,7 +38,7 @@ struct Group {
   long long sa[kMaxDims] = {0};   // stride in operand A (or 0 if absent)
   long long sb[kMaxDims] = {0};   // stride in operand B
   long long sc[kMaxDims] = {0};   // stride in the output
-  long long total() const {
+  __host__ __device__ long long total() const {
     long long t = 1;
     for (int i = 0; i < nd; ++i) t *= size[i];
     return t;

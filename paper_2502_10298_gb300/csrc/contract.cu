@@ -6,6 +6,8 @@
 // b, m, n, k is a group of tensor legs with arbitrary strides.  Index
 // permutations are therefore never materialised: a tile loader gathers
 // operand elements through per-tile offset tables kept in shared memory.
+#include <algorithm>
+
 #include "common.h"
 #include "kernels.h"
 #include "prof.h"
@@ -14,7 +16,8 @@ namespace sctm {
 
 template <typename T, typename Tc, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C) {
+contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
+                long long kchunk, double* __restrict__ W) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   __shared__ long long offAm[BM], offCm[BM], offBn[BN], offCn[BN];
@@ -58,12 +61,15 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = Tc(0);
 
-  for (long long k0 = 0; k0 < d.K; k0 += BK) {
+  // split K (gridDim.y > 1): this CTA sums k in [kb, ke) into the FP64 buffer W
+  const long long kb = (long long)blockIdx.y * kchunk;
+  const long long ke = min(d.K, kb + kchunk);
+  for (long long k0 = kb; k0 < ke; k0 += BK) {
     __syncthreads();
     if (tid < BK) {
       long long k = k0 + tid;
-      offAk[tid] = (k < d.K) ? group_offset(d.k, d.k.sa, k) : -1;
-      offBk[tid] = (k < d.K) ? group_offset(d.k, d.k.sb, k) : -1;
+      offAk[tid] = (k < ke) ? group_offset(d.k, d.k.sa, k) : -1;
+      offBk[tid] = (k < ke) ? group_offset(d.k, d.k.sb, k) : -1;
     }
     __syncthreads();
     for (int idx = tid; idx < BM * BK; idx += NT) {
@@ -106,6 +112,10 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
       int nn = tx + j * TX;
       long long on = offCn[nn];
       if (on < 0) continue;
+      if (W) {
+        atomicAdd(&W[(b * d.M + m0 + mm) * d.N + n0 + nn], (double)acc[i][j]);
+        continue;
+      }
       T v = alpha * (T)acc[i][j];
       if (d.beta != 0.0) v += beta * C[om + on];
       C[om + on] = v;
@@ -113,23 +123,77 @@ contract_kernel(ContractDesc d, const T* __restrict__ A, const T* __restrict__ B
   }
 }
 
-template <typename T>
-void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute) {
-  if (d.M == 0 || d.N == 0 || d.B == 0) return;
-  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
-  long long tiles = ((d.N + BN - 1) / BN) * ((d.M + BM - 1) / BM);
-  SCTM_CHECK(tiles < (1LL << 31) && d.B <= 65535, "contraction too large for grid");
-  dim3 grid((unsigned)tiles, 1, (unsigned)d.B);
-  // algorithmic work: 2 B M N K flops; bytes = operands read once + result written
-  ProfScope ps(PF_CONTRACT, s, 2.0 * d.B * d.M * d.N * d.K,
-               (double)sizeof(T) * d.B * (d.M * d.K + d.K * d.N + d.M * d.N * (d.beta != 0 ? 2 : 1)));
-  if (fp32_compute)
-    contract_kernel<T, float, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C);
-  else
-    contract_kernel<T, T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C);
+// C = alpha W + beta C through the output strides, W[b][m][n] (Wm x Wn per batch)
+__global__ void splitk_finish_kernel(ContractDesc d, long long Wm, long long Wn, const double* __restrict__ W,
+                                     double* __restrict__ C) {
+  const long long total = d.B * d.M * d.N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long n = idx % d.N, m = (idx / d.N) % d.M, b = idx / (d.N * d.M);
+    const long long off = group_offset(d.bat, d.bat.sc, b) + group_offset(d.m, d.m.sc, m) +
+                          group_offset(d.n, d.n.sc, n);
+    double v = d.alpha * W[(b * Wm + m) * Wn + n];
+    if (d.beta != 0.0) v += d.beta * C[off];
+    C[off] = v;
+  }
+}
+
+void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, const double* W, double* C,
+                          cudaStream_t s) {
+  const long long total = d.B * d.M * d.N;
+  if (total == 0) return;
+  ProfScope pf(PF_MISC, s, 0.0, 8.0 * total * (d.beta != 0 ? 3 : 2));
+  const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 148 * 16);
+  splitk_finish_kernel<<<blocks, 256, 0, s>>>(d, Wm, Wn, W, C);
   SCTM_CUDA(cudaGetLastError());
 }
 
-template void launch_contract<double>(const ContractDesc&, const double*, const double*, double*, cudaStream_t, bool);
+namespace {
+constexpr int kCBM = 64, kCBN = 64, kCBK = 16;
+// K splits for outputs with too few 64 x 64 tiles; at least 256 of K per split
+long long contract_splits(const ContractDesc& d) {
+  const long long tiles = ((d.M + kCBM - 1) / kCBM) * ((d.N + kCBN - 1) / kCBN) * d.B;
+  const long long want = (2 * 148 + tiles - 1) / tiles;
+  long long sp = std::min<long long>(want, d.K / 256);
+  if (sp < 2 || d.B > 65535) return 1;
+  return std::min<long long>(sp, 65535);
+}
+}  // namespace
+
+size_t contract_scratch_doubles(const ContractDesc& d) {
+  return contract_splits(d) > 1 ? (size_t)(d.B * d.M * d.N) + 32 : 0;
+}
+
+template <typename T>
+void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute,
+                     double* scratch) {
+  if (d.M == 0 || d.N == 0 || d.B == 0) return;
+  constexpr int BM = kCBM, BN = kCBN, BK = kCBK, TM = 4, TN = 4;
+  long long tiles = ((d.N + BN - 1) / BN) * ((d.M + BM - 1) / BM);
+  SCTM_CHECK(tiles < (1LL << 31) && d.B <= 65535, "contraction too large for grid");
+  const long long splits = scratch ? contract_splits(d) : 1;
+  const long long kchunk = splits > 1 ? (((d.K + splits - 1) / splits + BK - 1) / BK) * BK : d.K;
+  const long long nsplit = (d.K + kchunk - 1) / kchunk;
+  double* W = nullptr;
+  if (splits > 1) {
+    W = scratch;
+    SCTM_CUDA(cudaMemsetAsync(W, 0, (size_t)(d.B * d.M * d.N) * sizeof(double), s));
+  }
+  dim3 grid((unsigned)tiles, (unsigned)(splits > 1 ? nsplit : 1), (unsigned)d.B);
+  // algorithmic work: 2 B M N K flops; bytes = operands read once + result written
+  {
+    ProfScope ps(PF_CONTRACT, s, 2.0 * d.B * d.M * d.N * d.K,
+                 (double)sizeof(T) * d.B * (d.M * d.K + d.K * d.N + d.M * d.N * (d.beta != 0 ? 2 : 1)));
+    if (fp32_compute)
+      contract_kernel<T, float, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C, kchunk, W);
+    else
+      contract_kernel<T, T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(d, A, B, C, kchunk, W);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  if (W) launch_splitk_finish(d, d.M, d.N, W, C, s);
+}
+
+template void launch_contract<double>(const ContractDesc&, const double*, const double*, double*, cudaStream_t, bool,
+                                      double*);
 
 }  // namespace sctm

@@ -133,7 +133,8 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
 // P = 1 - U U^T, Q = 1 - V V^T the columns
 //   y_i = (s_i^2 - P M M^T P)^-1 P (s_i u_bar_i + M v_bar_i),
 //   z_i = (s_i^2 - Q M^T M Q)^-1 Q (M^T u_bar_i + s_i v_bar_i)
-// are found by column-wise conjugate gradients, which only apply M and M^T.
+// are found by column-wise conjugate gradients (cg_steps of them), which only
+// apply M and M^T; with cg_steps = 0 every column takes the leading term below.
 // Then
 //   M_bar = U X V^T + Y V^T + U Z^T,
 //   X = F o (J - J^T) S + diag(S_bar) + S F o (K - K^T), J = U^T U_bar, K = V^T V_bar,
@@ -145,11 +146,10 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
 // iteration stops where its operator is not safely positive definite (see
 // launch_cg_update); smaller kept values take the leading term
 // y_i = P u_bar_i / s_i, z_i = Q v_bar_i / s_i.  Columns without cotangent stay zero.
-static constexpr int kComplementCG = 10;
 static constexpr double kComplementMinRel = 1e-3;
 
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
-                                  const Tensor& V, double eps_l) {
+                                  const Tensor& V, double eps_l, int cg_steps) {
   const int k = S.shape[0];
   const int nb = U.shape[0];
   Tensor gU = no_grad(U), gV = no_grad(V), gS = no_grad(S);
@@ -171,6 +171,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
   einsum_into(c, "j,j->j", S, S, s2, 1.0, 0.0, false);   // s_j^2
   // masks: m_j = 1 for s_j >= kComplementMinRel s_1 (solved), else 0 (leading term)
   Tensor msk = spectrum_map(c, S, k, kComplementMinRel, 2);
+  if (cg_steps <= 0) launch_fill(k, 0.0, msk.data, c.stream);   // leading term for every column
   Tensor nmsk = c.empty({k});
   launch_fill(k, 1.0, nmsk.data, c.stream);
   launch_axpy(k, -1.0, msk.data, nmsk.data, c.stream);
@@ -183,7 +184,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
     Tensor rr = c.empty({k}), rr2 = c.empty({k}), pq = c.empty({k}), pp = c.empty({k});
     int* frozen = reinterpret_cast<int*>(c.zeros({(k + 1) / 2}).data);
     launch_coldot(nb, k, R.data, R.data, rr.data, c.stream);
-    for (int it = 0; it < kComplementCG; ++it) {
+    for (int it = 0; it < cg_steps; ++it) {
       Tensor Bp = project(Bas, left ? Mx(MTx(Pd)) : MTx(Mx(Pd)));
       Tensor Q = scale_dim(c, Pd, 1, s2);
       launch_axpy(Q.numel(), -1.0, Bp.data, Q.data, c.stream);          // Q = s^2 p - B p
@@ -198,14 +199,17 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
     return Yv;
   };
   // right-hand sides: P (U_bar S + M V_bar), Q (M^T U_bar + V_bar S)
-  Tensor bY = scale_dim(c, gU, 1, S);
-  launch_axpy(bY.numel(), 1.0, Mx(gV).data, bY.data, c.stream);
-  bY = project(U, bY);
-  Tensor bZ = scale_dim(c, gV, 1, S);
-  launch_axpy(bZ.numel(), 1.0, MTx(gU).data, bZ.data, c.stream);
-  bZ = project(V, bZ);
-  Tensor A = solve(U, scale_dim(c, bY, 1, msk), true);
-  Tensor Bm = solve(V, scale_dim(c, bZ, 1, msk), false);
+  Tensor bY, bZ;
+  if (cg_steps > 0) {
+    bY = scale_dim(c, gU, 1, S);
+    launch_axpy(bY.numel(), 1.0, Mx(gV).data, bY.data, c.stream);
+    bY = project(U, bY);
+    bZ = scale_dim(c, gV, 1, S);
+    launch_axpy(bZ.numel(), 1.0, MTx(gU).data, bZ.data, c.stream);
+    bZ = project(V, bZ);
+  }
+  Tensor A = cg_steps > 0 ? solve(U, scale_dim(c, bY, 1, msk), true) : c.zeros({nb, k});
+  Tensor Bm = cg_steps > 0 ? solve(V, scale_dim(c, bZ, 1, msk), false) : c.zeros({nb, k});
   // leading terms for the unmasked columns: P U_bar S^-1, Q V_bar S^-1
   {
     Tensor w = c.empty({k});
@@ -267,10 +271,11 @@ static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, c
     if (tap) {
       Tensor rT = rhoT, rB = rhoB, U = Ur, S = Sr, V = Vr;
       double eps = P.eps_l;
-      c.tape.push([&c, rT, rB, U, S, V, eps]() {
+      int cg = P.adjoint_cg_steps;
+      c.tape.push([&c, rT, rB, U, S, V, eps, cg]() {
         bool t2 = c.tape.active;
         c.tape.active = false;
-        truncated_svd_adjoint(c, rT, rB, U, S, V, eps);
+        truncated_svd_adjoint(c, rT, rB, U, S, V, eps, cg);
         c.tape.active = t2;
       });
     }

@@ -32,6 +32,7 @@ struct Params {
   double eps_l = 1e-36;       // Lorentzian broadening (relative to s_max^4)
   bool mixed = false;         // mixed mode: FP32 contractions, randomized projectors
   int power_steps = 2;        // randomized projectors: power steps (mixed mode)
+  int adjoint_cg_steps = 0;   // randomized projectors' adjoint: CG steps for the complement coupling
   int randomized_min = 256;   // randomized projectors only when the truncated space has >= this dimension
 };
 

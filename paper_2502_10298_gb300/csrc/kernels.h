@@ -5,8 +5,16 @@
 namespace sctm {
 
 // fp32_compute: operands rounded to FP32 on load, FP32 accumulation (mixed mode)
+// scratch: contract_scratch_doubles(d) doubles (may be null: no K split).  Outputs
+// with few 64 x 64 tiles and a long K are then split over K into an FP64
+// buffer and finished by launch_splitk_finish.
 template <typename T>
-void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute);
+void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute,
+                     double* scratch = nullptr);
+size_t contract_scratch_doubles(const ContractDesc& d);
+// C = alpha W + beta C through the output strides of d; W[b][m][n] with Wm x Wn per batch
+void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, const double* W, double* C,
+                          cudaStream_t s);
 
 // Tensor-core form of the same contraction (mixed mode): operands split into
 // TF32 hi/lo pairs, 3xTF32 tcgen05 MMAs with FP32 accumulation, FP64 output.
@@ -73,6 +81,15 @@ void launch_dot(int batch, long long n, const double* x, const double* y, long l
                 double* out, double* partial, cudaStream_t s);
 
 void launch_fill(long long n, double v, double* x, cudaStream_t s);
+
+// y += a[0] * x with the scalar a on the device
+void launch_axpy_dev(long long n, const double* a, const double* x, double* y, cudaStream_t s);
+// out[g] = in[g] * v[j] + beta * out[g], j = index of dimension `dim` of g (.sa = in, .sc = out strides)
+void launch_scale_dim(const Group& g, int dim, const double* in, const double* v, double beta, double* out,
+                      cudaStream_t s);
+// vbar[j] += sum over g with index j in dimension `dim` of a[g] b[g] (.sa = a, .sb = b strides)
+void launch_scale_dim_reduce(const Group& g, int dim, const double* a, const double* b, double* vbar,
+                             cudaStream_t s);
 
 // Column-wise conjugate gradient on rows x r blocks (row-major), one shifted
 // system (s_j^2 - B) y_j = b_j per column: update Y += a P, R -= a Q with

@@ -1,5 +1,7 @@
 // Small memory-bound kernels of the engine: strided copies, row/column
 // scaling, spectrum maps, sign fixing, max-abs rescaling and dot products.
+#include <algorithm>
+
 #include "common.h"
 #include "kernels.h"
 #include "prof.h"
@@ -318,6 +320,85 @@ void launch_gaussian(long long rows, long long cols, unsigned long long seed, do
   if (n == 0) return;
   ProfScope ps_(PF_MISC, s, 0.0, 0.0);
   gaussian_kernel<<<grid_for(n), kThreads, 0, s>>>(n, seed, X);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- scaling
+__global__ void axpy_dev_kernel(long long n, const double* __restrict__ a, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  const double av = a[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(av, x[i], y[i]);
+}
+
+void launch_axpy_dev(long long n, const double* a, const double* x, double* y, cudaStream_t s) {
+  if (n == 0) return;
+  ProfScope ps_(PF_MISC, s, 2.0 * n, 24.0 * n);
+  axpy_dev_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// out[g] = in[g] * v[index of dim `dim`] + beta * out[g] over the group g (strides .sa = in, .sc = out)
+__global__ void scale_dim_kernel(Group g, long long total, int dim, const double* __restrict__ in,
+                                 const double* __restrict__ v, double beta, double* __restrict__ out) {
+  long long inner = 1;
+  for (int i = g.nd - 1; i > dim; --i) inner *= g.size[i];
+  const long long sz = g.size[dim];
+  for (long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x; lin < total;
+       lin += (long long)gridDim.x * blockDim.x) {
+    const long long oi = group_offset(g, g.sa, lin), oo = group_offset(g, g.sc, lin);
+    double r = in[oi] * v[(lin / inner) % sz];
+    if (beta != 0.0) r += beta * out[oo];
+    out[oo] = r;
+  }
+}
+
+void launch_scale_dim(const Group& g, int dim, const double* in, const double* v, double beta, double* out,
+                      cudaStream_t s) {
+  const long long total = g.total();
+  if (total == 0) return;
+  ProfScope ps_(PF_MISC, s, (double)total, 24.0 * total);
+  scale_dim_kernel<<<grid_for(total), kThreads, 0, s>>>(g, total, dim, in, v, beta, out);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// vbar[j] += sum over the other indices of a[g] * b[g] with j the index of dim
+// `dim` (strides .sa = a, .sb = b); grid.y splits the work, one atomic per block
+__global__ void scale_dim_reduce_kernel(Group g, int dim, const double* __restrict__ a, const double* __restrict__ b,
+                                        double* __restrict__ vbar) {
+  long long inner = 1;
+  for (int i = g.nd - 1; i > dim; --i) inner *= g.size[i];
+  const long long sz = g.size[dim];
+  const long long per_j = g.total() / sz;   // (outer x inner) entries per index j
+  const long long j = blockIdx.x;
+  double acc = 0.0;
+  for (long long t = blockIdx.y * (long long)blockDim.x + threadIdx.x; t < per_j;
+       t += (long long)gridDim.y * blockDim.x) {
+    const long long o = t / inner, i = t % inner;
+    const long long lin = (o * sz + j) * inner + i;
+    acc = fma(a[group_offset(g, g.sa, lin)], b[group_offset(g, g.sb, lin)], acc);
+  }
+  __shared__ double red[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    atomicAdd(&vbar[j], t);
+  }
+}
+
+void launch_scale_dim_reduce(const Group& g, int dim, const double* a, const double* b, double* vbar,
+                             cudaStream_t s) {
+  const long long total = g.total();
+  if (total == 0) return;
+  ProfScope ps_(PF_MISC, s, 2.0 * total, 16.0 * total);
+  const long long sz = g.size[dim];
+  const long long per_j = total / sz;
+  const unsigned ys = (unsigned)std::max<long long>(1, std::min<long long>((per_j + kThreads - 1) / kThreads,
+                                                                           (152 * 8 + sz - 1) / sz));
+  scale_dim_reduce_kernel<<<dim3((unsigned)sz, ys), kThreads, 0, s>>>(g, dim, a, b, vbar);
   SCTM_CUDA(cudaGetLastError());
 }
 

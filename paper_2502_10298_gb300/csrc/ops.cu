@@ -193,7 +193,11 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
     launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32);
     c.arena.release(mk);   // stream-ordered: later work on the stream reuses it after the GEMM
   } else {
-    launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute);
+    const size_t wn = contract_scratch_doubles(d);
+    size_t mk = c.arena.mark();
+    double* scratch = wn ? c.arena.alloc((long long)wn) : nullptr;
+    launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute, scratch);
+    c.arena.release(mk);
   }
   if (prof_enabled()) prof_set_tag("");
   if (!record || !c.tape.active || !C.grad) return;
@@ -326,13 +330,28 @@ Tensor spectrum_map(Ctx& c, const Tensor& S, int kout, double cutoff, int mode) 
 }
 
 Tensor scale_dim(Ctx& c, const Tensor& X, int dim, const Tensor& v) {
-  SCTM_CHECK(X.nd <= 6 && dim < X.nd && v.nd == 1 && v.shape[0] == X.shape[dim], "scale_dim shape");
-  char sx[8] = {0}, sy[8] = {0}, sv[2] = {0};
-  const char* L = "abcdef";
-  for (int i = 0; i < X.nd; ++i) sx[i] = L[i], sy[i] = L[i];
-  sv[0] = L[dim];
-  std::string spec = std::string(sx) + "," + sv + "->" + sy;
-  return einsum(c, spec.c_str(), X, v, 1.0);
+  SCTM_CHECK(dim < X.nd && v.nd == 1 && v.shape[0] == X.shape[dim], "scale_dim shape");
+  Tensor Y = c.empty_shape(X.shape, X.nd);
+  Group g;
+  g.nd = X.nd;
+  for (int i = 0; i < X.nd; ++i) g.size[i] = X.shape[i], g.sa[i] = X.stride[i], g.sc[i] = Y.stride[i];
+  launch_scale_dim(g, dim, X.data, v.data, 0.0, Y.data, c.stream);
+  if (c.tape.active && Y.grad && (X.grad || v.grad)) {
+    Tensor x = X, vv = v, y = Y;
+    c.tape.push([&c, x, vv, y, dim]() {
+      Group h;
+      h.nd = x.nd;
+      for (int i = 0; i < x.nd; ++i) h.size[i] = x.shape[i], h.sa[i] = y.stride[i], h.sc[i] = x.stride[i];
+      if (x.grad) launch_scale_dim(h, dim, y.grad, vv.data, 1.0, x.grad, c.stream);   // xbar += ybar v
+      if (vv.grad) {
+        Group r;   // vbar[j] += sum ybar x
+        r.nd = x.nd;
+        for (int i = 0; i < x.nd; ++i) r.size[i] = x.shape[i], r.sa[i] = y.stride[i], r.sb[i] = x.stride[i];
+        launch_scale_dim_reduce(r, dim, y.grad, x.data, vv.grad, c.stream);
+      }
+    });
+  }
+  return Y;
 }
 
 Tensor row_signs(Ctx& c, const Tensor& P) {
@@ -379,11 +398,10 @@ Tensor dot(Ctx& c, const Tensor& X_in, const Tensor& Y_in) {
     Tensor x = X, y = Y, oo = o;
     c.tape.push([&c, x, y, oo]() {
       // xbar += obar * y ; ybar += obar * x   (obar read on device)
-      int n = (int)x.numel();
-      Tensor xv = x.reshape({n, 1}), yv = y.reshape({n, 1});
-      Tensor ob = grad_view(oo).reshape({1});
-      if (x.grad) einsum_into(c, "iz,z->i", yv, ob, grad_view(x.reshape({n})), 1.0, 1.0, false);
-      if (y.grad) einsum_into(c, "iz,z->i", xv, ob, grad_view(y.reshape({n})), 1.0, 1.0, false);
+      const long long n = x.numel();
+      const double* ob = oo.grad;   // obar, on the device
+      if (x.grad) launch_axpy_dev(n, ob, y.data, x.grad, c.stream);
+      if (y.grad) launch_axpy_dev(n, ob, x.data, y.grad, c.stream);
     });
   }
   return o;

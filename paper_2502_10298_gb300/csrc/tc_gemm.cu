@@ -23,6 +23,8 @@
 // issued and returns, so the host sees an error instead of a hung context.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "common.h"
 #include "kernels.h"
 #include "prof.h"
@@ -190,7 +192,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(TC_THREADS_V2, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcEpi e,
-                   int nk, double* __restrict__ C, int* status) {
+                   int nk_total, int slabs_per_split, double* __restrict__ C, double* __restrict__ W,
+                   long long Wm, long long Wn, int* status) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
@@ -209,6 +212,9 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
   const int m_tile = first_m + (t % (GM * e.num_n)) % gsz;
   const int n_tile = (t % (GM * e.num_n)) / gsz;
   const long long m0 = (long long)m_tile * TC_BM, n0 = (long long)n_tile * TC_BN;
+  // split K: this CTA accumulates slabs [s0, s0 + nk) into the FP64 buffer W
+  const int s0 = blockIdx.z * slabs_per_split;
+  const int nk = min(nk_total - s0, slabs_per_split);
 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
         uint8_t* sp = base + st * TC_STAGE;
         mbar_expect_tx(&full[st], TC_STAGE);
         issued_parity[st] = (s / TC_STAGES) & 1;
-        const int kc = s * TC_BK;
+        const int kc = (s0 + s) * TC_BK;
         tma_load_4d(sp, &mapA, &full[st], kc, (int)m0, b, 0);
         tma_load_4d(sp + TC_TILE_A, &mapA, &full[st], kc, (int)m0, b, 1);
         tma_load_4d(sp + 2 * TC_TILE_A, &mapB, &full[st], kc, (int)n0, b, 0);
@@ -331,6 +337,11 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
         const int r = idx / TC_BN, cn = idx % TC_BN;
         const long long oc = offCm[r], on = offCn[cn];
         if (oc < 0 || on < 0) continue;
+        if (W) {
+          // partial sum of this K range; splitk_finish_kernel applies alpha, beta
+          atomicAdd(&W[((long long)b * Wm + m0 + r) * Wn + n0 + cn], tile[r * (TC_BN + 1) + cn]);
+          continue;
+        }
         double v = e.alpha * tile[r * (TC_BN + 1) + cn];
         if (e.beta != 0.0) v += e.beta * C[oc + on];
         C[oc + on] = v;
@@ -404,9 +415,23 @@ bool tc_eligible(const ContractDesc& d) {
          2.0 * d.B * d.M * d.N * d.K >= 1e8 && round_up(d.M, TC_BM) / TC_BM * (round_up(d.N, TC_BN) / TC_BN) < (1LL << 31);
 }
 
+// K splits: only when the output has too few tiles to fill the GPU; at least
+// 4 slabs (128 of K) per split
+static int tc_splits(const ContractDesc& d) {
+  const long long tiles = (round_up(d.M, TC_BM) / TC_BM) * (round_up(d.N, TC_BN) / TC_BN) * d.B;
+  const long long nk = round_up(d.K, TC_BK) / TC_BK;
+  const long long want = (2 * 148 + tiles - 1) / tiles;
+  long long sp = std::min<long long>(want, nk / 4);
+  if (sp < 2) return 1;
+  const long long per = (nk + sp - 1) / sp;
+  return (int)((nk + per - 1) / per);
+}
+
 size_t tc_scratch_floats(const ContractDesc& d) {
-  const long long Kp = round_up(d.K, TC_BK);
-  return (size_t)2 * d.B * Kp * (round_up(d.M, TC_BM) + round_up(d.N, TC_BN)) + 64;
+  const long long Kp = round_up(d.K, TC_BK), Mp = round_up(d.M, TC_BM), Np = round_up(d.N, TC_BN);
+  size_t f = (size_t)2 * d.B * Kp * (Mp + Np) + 64;
+  if (tc_splits(d) > 1) f += (size_t)2 * d.B * Mp * Np + 64;   // FP64 partial sums
+  return f;
 }
 
 void launch_contract_tc(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
@@ -451,13 +476,25 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
     SCTM_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr = true;
   }
-  dim3 grid((unsigned)((long long)e.num_m * e.num_n), (unsigned)d.B);
+  const int nk = (int)(Kp / TC_BK);
+  const int splits = tc_splits(d);
+  const int per = (nk + splits - 1) / splits;
+  double* W = nullptr;
+  if (splits > 1) {
+    W = reinterpret_cast<double*>(pb + 2 * d.B * Np * Kp + 32);   // 128-byte aligned (offsets are multiples of 32 floats)
+    W = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(W) + 255) & ~uintptr_t(255));
+    SCTM_CUDA(cudaMemsetAsync(W, 0, (size_t)d.B * Mp * Np * sizeof(double), s));
+  }
+  dim3 grid((unsigned)((long long)e.num_m * e.num_n), (unsigned)d.B, (unsigned)splits);
   // algorithmic work 2 B M N K (the tensor pipe executes three TF32 products
   // per multiply-add); bytes: the hi/lo panels read once, the FP64 result written
-  ProfScope ps(PF_TENSOR, s, 2.0 * d.B * d.M * d.N * d.K,
-               8.0 * d.B * Kp * (Mp + Np) + 8.0 * d.B * d.M * d.N * (d.beta != 0 ? 2 : 1));
-  tc_gemm_kernel<<<grid, TC_THREADS_V2, TC_SMEM, s>>>(mA, mB, e, (int)(Kp / TC_BK), C, status);
-  SCTM_CUDA(cudaGetLastError());
+  {
+    ProfScope ps(PF_TENSOR, s, 2.0 * d.B * d.M * d.N * d.K,
+                 8.0 * d.B * Kp * (Mp + Np) + 8.0 * d.B * d.M * d.N * (d.beta != 0 ? 2 : 1));
+    tc_gemm_kernel<<<grid, TC_THREADS_V2, TC_SMEM, s>>>(mA, mB, e, nk, per, C, W, Mp, Np, status);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  if (W) launch_splitk_finish(d, Mp, Np, W, C, s);
 }
 
 }  // namespace sctm
