@@ -140,6 +140,27 @@ SCTM_API int sctm_get_env(sctm_handle h, int x, int y, double* out_dev);
 SCTM_API int sctm_svd(sctm_handle h, int m, int n, const double* M_dev, double* U_dev, double* S_dev,
                       double* V_dev);
 
+/* The Jacobi SVD of sctm_svd without a handle and without any allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not allocate device memory while they run -- inside a region where
+ * allocation is forbidden or unsafe (work being captured into a CUDA graph on
+ * their stream, an allocator callback, a loop with a fixed memory budget) --
+ * and that hold no engine handle.  Its scratch is one statically sized device
+ * array per device (16 MiB + 8 KiB), so:
+ *  - sizes are limited to (m + n) * n <= 2^21 (e.g. m = n = 1024); larger
+ *    matrices return SCTM_ERR_ARG without touching the device;
+ *  - calls that overlap in time on one device (two streams, two host threads)
+ *    race on that scratch: serialise them;
+ *  - the first call on each device looks up the array's address and the
+ *    kernel's occupancy; make it before any stream capture begins.
+ * Arguments as for sctm_svd (m >= n, device buffers owned by the caller);
+ * stream is a cudaStream_t (NULL = legacy default stream).  The call
+ * synchronises that stream and returns SCTM_OK, SCTM_ERR_ARG, SCTM_ERR_CUDA or
+ * SCTM_ERR_SVD_NOCONV (sweep limit reached).  With sctm_profile recording,
+ * the launch is timed with events like every other launch. */
+SCTM_API int sctm_svd_noalloc(int m, int n, const double* M_dev, double* U_dev, double* S_dev, double* V_dev,
+                              void* stream);
+
 /* Tensor contraction C = alpha * einsum(spec, A, B) + beta * C on the handle's
  * stream, in the handle's precision: the primitive under every absorption,
  * rho network and projector application (Sec. II.B).  spec is an einsum string

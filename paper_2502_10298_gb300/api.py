@@ -10,7 +10,7 @@ import torch
 __all__ = [
     "load_library", "Config", "sctm_create", "sctm_destroy", "split_ctmrg_init", "split_ctmrg_move",
     "split_ctmrg_sweeps", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
-    "sctm_get_env", "sctm_workspace_high_water", "sctm_profile", "sctm_svd", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
+    "sctm_get_env", "sctm_workspace_high_water", "sctm_profile", "sctm_svd", "sctm_svd_noalloc", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH):
         "sctm_profile": (i, [vp, i, _dp]),
         "sctm_svd": (i, [vp, i, i, vp, vp, vp, vp]),
         "sctm_einsum": (i, [vp, ctypes.c_char_p, vp, _ip, vp, _ip, vp, _ip, d, d]),
+        "sctm_svd_noalloc": (i, [i, i, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +213,23 @@ def sctm_einsum(h, spec: str, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor 
     sa, sb, sc = shp(A), shp(B), shp(C)
     _check(h, _lib.sctm_einsum(h, spec.encode(), _dev(A), sa, _dev(B), sb, _dev(C), sc, float(alpha), float(beta)))
     return C
+
+
+def sctm_svd_noalloc(M: torch.Tensor, U=None, S=None, V=None):
+    """(U, S, V) of a CUDA float64 matrix (rows >= columns, (m + n) n <= 2^21)
+    through the handle-free entry point that allocates no device memory; the
+    output buffers may be passed in (e.g. preallocated before a capture)."""
+    load_library()
+    m, n = M.shape
+    assert M.is_contiguous()
+    U = torch.empty((m, n), dtype=torch.float64, device=M.device) if U is None else U
+    S = torch.empty((n,), dtype=torch.float64, device=M.device) if S is None else S
+    V = torch.empty((n, n), dtype=torch.float64, device=M.device) if V is None else V
+    rc = _lib.sctm_svd_noalloc(m, n, _dev(M), _dev(U), _dev(S), _dev(V),
+                               ctypes.c_void_p(torch.cuda.current_stream(M.device).cuda_stream))
+    if rc != 0:
+        raise SctmError(rc, "sctm_svd_noalloc failed")
+    return U, S, V
 
 
 def sctm_workspace_high_water(h) -> int:
