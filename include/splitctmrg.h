@@ -65,7 +65,9 @@ typedef struct {
                                truncated space exceeds 2 chi and randomized_min;
                                decompositions and Gram matrices in FP64; default
                                cutoff 1e-6.
-                            2: as 1 with every contraction on the CUDA cores (FP32). */
+                            2: as 1 with every contraction on the CUDA cores (FP32).
+                            3: FP64 arithmetic throughout with the randomized
+                               projectors of 1 (cutoff default 1e-6). */
   double svd_cutoff;     /* relative singular-value cutoff of projectors (<=0: 1e-8) */
   double lorentz_eps;    /* Lorentzian broadening of the SVD adjoint (<=0: 1e-36 s_max^4) */
   size_t workspace_bytes;/* device workspace; 0 = library default          */
@@ -78,6 +80,10 @@ typedef struct {
                             leading-order coupling to the unresolved spectrum;
                             n > 0 = n conjugate-gradient steps on the first-order
                             coupling (experimental)                                */
+  int adjoint_band;      /* mixed mode, reverse pass of randomized projectors: 0 = all
+                            2 chi computed triplets coupled exactly; n > 0 = only the
+                            first chi + n - 1 (the rest of the spectrum is treated
+                            as the complement)                                      */
 } sctm_config;
 
 /* Create a handle.  stream: a cudaStream_t (NULL = legacy default stream). */

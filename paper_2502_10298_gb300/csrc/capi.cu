@@ -246,11 +246,11 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
   int rc = guard(h.get(), [&]() {
     SCTM_CHECK(cfg->Lx >= 1 && cfg->Ly >= 1 && cfg->p >= 1 && cfg->D >= 1 && cfg->chi >= 1, "bad dimensions");
     SCTM_CHECK(cfg->D * cfg->D <= cfg->chi, "chi must be >= D^2");
-    SCTM_CHECK(cfg->precision >= 0 && cfg->precision <= 2, "precision must be 0 (FP64), 1 or 2 (mixed)");
+    SCTM_CHECK(cfg->precision >= 0 && cfg->precision <= 3, "precision must be 0 (FP64), 1, 2 (mixed) or 3");
     Params& P = h->P;
     P.Lx = cfg->Lx, P.Ly = cfg->Ly, P.p = cfg->p, P.D = cfg->D, P.chi = cfg->chi;
-    P.mixed = (cfg->precision >= 1);
-    h->c.fp32_compute = P.mixed;
+    P.mixed = (cfg->precision >= 1);   // randomized projectors for large truncated spaces
+    h->c.fp32_compute = (cfg->precision == 1 || cfg->precision == 2);
     h->c.tensor_cores = (cfg->precision == 1);
     if (P.mixed) P.cutoff = 1e-6;   // FP32 contractions: singular values below ~1e-7 s_max are rounding noise
     if (cfg->svd_cutoff > 0) P.cutoff = cfg->svd_cutoff;
@@ -259,6 +259,8 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     if (cfg->randomized_min > 0) P.randomized_min = cfg->randomized_min;
     SCTM_CHECK(cfg->adjoint_cg_steps >= 0 && cfg->adjoint_cg_steps <= 64, "adjoint_cg_steps must be in [0, 64]");
     P.adjoint_cg_steps = cfg->adjoint_cg_steps;
+    SCTM_CHECK(cfg->adjoint_band >= 0, "adjoint_band must be >= 0");
+    P.adjoint_band = cfg->adjoint_band > 0 ? cfg->adjoint_band - 1 : -1;
     if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
     h->c.stream = (cudaStream_t)stream;
     const int chi = P.chi, D = P.D;

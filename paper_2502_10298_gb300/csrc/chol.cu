@@ -6,6 +6,8 @@
 // of R is set to zero and the matching column of Q = Y R^+ comes out zero, so
 // Q always has orthonormal or zero columns (rank-deficient sketches of
 // zero-padded environments are the common case).
+#include <cstdio>
+
 #include "common.h"
 #include "kernels.h"
 #include "prof.h"
@@ -82,6 +84,9 @@ __global__ void __launch_bounds__(32 * kTriWarps) tri_inv_kernel(int r, const do
 void launch_chol_qr_factor(int r, int batch, double* G, double* T, double tol_rel, cudaStream_t s) {
   if (batch == 0 || r == 0) return;
   SCTM_CHECK(r <= 2048, "Cholesky factor larger than 2048");
+  char tag[64] = {0};
+  if (prof_enabled()) std::snprintf(tag, sizeof(tag), "cholesky r%d batch%d", r, batch);
+  ProfTag profile_label(prof_enabled() ? tag : nullptr);
   {
     ProfScope ps(PF_SVD, s, (double)batch * r * (double)r * r / 3.0, (double)batch * 16.0 * r * r);
     chol_drop_kernel<<<batch, kCholThreads, 0, s>>>(r, G, tol_rel);

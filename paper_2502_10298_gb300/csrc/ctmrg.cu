@@ -62,15 +62,17 @@ static Tensor gram64(Ctx& c, const Tensor& Y) {
 }
 
 // Orthonormal (or zero) columns spanning the columns of each Y_i (m_i x r):
-// two passes of Cholesky QR (CholeskyQR2; Yamamoto et al. 2015) with FP64
-// Gram matrices and deflation of dependent columns (pivots below 1e-13 of the
-// largest), Q = Y R^+.  Not taped.
-static std::vector<Tensor> orthonormal_columns_batch(Ctx& c, const std::vector<Tensor>& Ys) {
+// Cholesky QR with FP64 Gram matrices and deflation of dependent columns
+// (pivots below 1e-13 of the largest), Q = Y R^+.  Two passes (CholeskyQR2;
+// Yamamoto et al. 2015) give orthonormality to rounding for condition numbers
+// up to about 1e8; one pass suffices for the intermediate bases of the power
+// iteration, which only have to keep the directions apart.  Not taped.
+static std::vector<Tensor> orthonormal_columns_batch(Ctx& c, const std::vector<Tensor>& Ys, int passes = 2) {
   const int nb = (int)Ys.size();
   if (nb == 0) return {};
   const int r = Ys[0].shape[1];
   std::vector<Tensor> Q = Ys;
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     Tensor Gb = c.empty({nb, r, r}), Tb = c.empty({nb, r, r});
     for (int i = 0; i < nb; ++i) copy_into(c, gram64(c, Q[i]), Gb.sub(0, i));
     launch_chol_qr_factor(r, nb, Gb.data, Tb.data, 1e-13, c.stream);
@@ -83,9 +85,8 @@ static std::vector<Tensor> orthonormal_columns_batch(Ctx& c, const std::vector<T
 // randomized subspace iteration (Halko, Martinsson, Tropp 2011, Alg. 4.4):
 // Q = orth(M Omega), then `power_steps` times Z = orth(M^T Q), Q = orth(M Z)
 // (a basis after every product keeps the small directions resolvable), and
-// finally B = Q^T M decomposed through its FP64 Gram matrix B B^T = W L W^T:
-// U = Q W, S = L^1/2, V = B^T W S^-1.  Returns U (beta x r), S (r), V (beta x r)
-// with M ~ U S V^T.  Not taped.
+// finally B = Q^T M decomposed as below.  Returns U (beta x r), S (r),
+// V (beta x r) with M ~ U S V^T.  Not taped.
 struct Trunc {
   Tensor U, S, V;
 };
@@ -99,29 +100,38 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
     launch_gaussian(b, r, 0x5eedULL + (unsigned long long)b * 131 + r, Om.data, c.stream);
     Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Om));       // M Omega
   }
-  std::vector<Tensor> Q = orthonormal_columns_batch(c, Y);
+  std::vector<Tensor> Q = orthonormal_columns_batch(c, Y, power_steps > 0 ? 1 : 2);
   for (int q = 0; q < power_steps; ++q) {
     for (size_t i = 0; i < nb; ++i)
       Y[i] = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));    // M^T Q
-    std::vector<Tensor> Z = orthonormal_columns_batch(c, Y);
+    std::vector<Tensor> Z = orthonormal_columns_batch(c, Y, 1);
     for (size_t i = 0; i < nb; ++i)
       Y[i] = einsum(c, "ab,bj->aj", rB[i], einsum(c, "ab,bj->aj", rT[i], Z[i]));    // M Z
-    Q = orthonormal_columns_batch(c, Y);
+    Q = orthonormal_columns_batch(c, Y, q + 1 < power_steps ? 1 : 2);   // the final basis: two passes
   }
-  std::vector<Tensor> Bt(nb), G(nb);
-  for (size_t i = 0; i < nb; ++i) {
+  // B^T = M^T Q = Q_B R_B (CholeskyQR2), R_B = U_R S V_R^T (FP64 Jacobi):
+  // M ~ Q B = (Q V_R) S (Q_B U_R)^T with both factors orthonormal and no
+  // division by small singular values (which would carry the contraction
+  // rounding into V and spoil the reverse pass)
+  std::vector<Tensor> Bt(nb);
+  for (size_t i = 0; i < nb; ++i)
     Bt[i] = einsum(c, "ba,bj->aj", rT[i], einsum(c, "ba,bj->aj", rB[i], Q[i]));    // B^T = M^T Q
-    G[i] = gram64(c, Bt[i]);                                                      // B B^T
+  std::vector<Tensor> QB = orthonormal_columns_batch(c, Bt, 2);
+  std::vector<Tensor> RB(nb);
+  {
+    Fp64Scope f(c);
+    for (size_t i = 0; i < nb; ++i) RB[i] = einsum(c, "ai,aj->ij", QB[i], Bt[i]);   // R_B = Q_B^T B^T
   }
-  std::vector<SVDResult> e = svd_batch(c, G);
+  std::vector<SVDResult> e = svd_batch(c, RB);
   std::vector<Trunc> out(nb);
   for (size_t i = 0; i < nb; ++i) {
-    out[i].S = spectrum_map(c, e[i].S, r, 0.0, 1);                                 // sqrt(lambda)
-    // lambda^-1/2; eigenvalues of the FP64 Gram matrix below 1e-14 lambda_max
-    // are rounding noise (singular values below 1e-7 s_max, under every cutoff)
-    Tensor sinv = spectrum_map(c, e[i].S, r, 1e-14, 0);
-    out[i].U = einsum(c, "ai,ij->aj", Q[i], e[i].V);
-    out[i].V = scale_dim(c, einsum(c, "ai,ij->aj", Bt[i], e[i].V), 1, sinv);
+    // singular vectors of rounding-level values (below 1e-10 s_1, far under any
+    // cutoff) are not resolved: zero them, so the reverse pass treats those
+    // directions as part of the complement
+    Tensor keep = spectrum_map(c, e[i].S, r, 1e-10, 2);
+    out[i].S = e[i].S;
+    out[i].U = scale_dim(c, einsum(c, "ai,ij->aj", Q[i], e[i].V), 1, keep);
+    out[i].V = scale_dim(c, einsum(c, "ai,ij->aj", QB[i], e[i].U), 1, keep);
   }
   return out;
 }
@@ -150,6 +160,10 @@ static constexpr double kComplementMinRel = 1e-3;
 
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l, int cg_steps) {
+  // FP64 arithmetic throughout: the complement terms divide P U_bar by s_i,
+  // and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level rounding of it,
+  // amplified by 1/s_i up to the inverse cutoff, swamps the gradient
+  Fp64Scope f64(c);
   const int k = S.shape[0];
   const int nb = U.shape[0];
   Tensor gU = no_grad(U), gV = no_grad(V), gS = no_grad(S);
@@ -269,7 +283,14 @@ static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, c
     Vk.shape[1] = k;
     Sk.shape[0] = k;
     if (tap) {
+      // the reverse pass couples the kept triplets exactly to the next
+      // `adjoint_band` computed ones (all r by default); the rest of the
+      // spectrum is treated as the complement
+      const int kb = P.adjoint_band < 0 ? (int)Sr.shape[0] : std::min((int)Sr.shape[0], k + P.adjoint_band);
       Tensor rT = rhoT, rB = rhoB, U = Ur, S = Sr, V = Vr;
+      U.shape[1] = kb;
+      V.shape[1] = kb;
+      S.shape[0] = kb;
       double eps = P.eps_l;
       int cg = P.adjoint_cg_steps;
       c.tape.push([&c, rT, rB, U, S, V, eps, cg]() {

@@ -11,6 +11,7 @@
 // One CTA owns one matrix of the batch.  Small matrices (n <= kSmemN) live in
 // shared memory; larger ones in a global workspace (kept in L2).
 #include <algorithm>
+#include <cstdio>
 #include <cooperative_groups.h>
 
 #include "common.h"
@@ -313,6 +314,10 @@ void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, 
                 int* status, cudaStream_t s, double noise_rel) {
   if (batch == 0 || n == 0) return;
   SCTM_CHECK(m >= n, "svd expects rows >= columns");
+  char tag[96] = {0};
+  if (prof_enabled())
+    std::snprintf(tag, sizeof(tag), "jacobi m%d n%d batch%d%s", m, n, batch, fits_smem(m, n) ? " smem" : " coop");
+  ProfTag profile_label(prof_enabled() ? tag : nullptr);
   const int max_sweeps = 60;
   const double tol = 2.3e-16 * 4.0 * sqrt((double)m);
   const int in_smem = fits_smem(m, n);

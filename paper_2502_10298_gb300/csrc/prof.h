@@ -18,6 +18,14 @@ bool prof_enabled();
 // out: PF_N rows of {milliseconds, launches, flops, bytes}
 void prof_collect(double* out);
 
+// sets a label for the scopes of the current block and clears it on exit
+struct ProfTag {
+  explicit ProfTag(const char* tag) {
+    if (tag) prof_set_tag(tag);
+  }
+  ~ProfTag() { prof_set_tag(""); }
+};
+
 struct ProfScope {
   // launches: kernel launches inside the scope
   ProfScope(int family, cudaStream_t s, double flops, double bytes, int launches = 1);

@@ -14,7 +14,7 @@
 //     a 3-stage shared-memory ring; one thread issues tcgen05.mma kind::tf32
 //     for A_hi B_hi + A_hi B_lo + A_lo B_hi (the 3xTF32 split: the dropped
 //     A_lo B_lo term is 2^-22 relative) into FP32 accumulators in tensor
-//     memory, one K slab at a time; eight warps read every slab's partial sums
+//     memory, two K slabs at a time; eight warps read every chunk's partial sums
 //     with tcgen05.ld, add them into FP32 register sums, and finally write
 //     alpha * sum (+ beta * C) in FP64 through the output strides.
 //
@@ -170,14 +170,15 @@ struct TcEpi {
 // Warp roles: warp 0 lane 0 issues TMA, warp 1 owns tensor memory and its
 // lane 0 issues the MMAs, warps 2..9 drain the accumulators.  Tensor memory
 // (512 columns): two buffers x {main = A_hi B_hi, corr = A_hi B_lo + A_lo B_hi}
-// x 128 columns.  Every K slab is accumulated afresh in one buffer; the drain
-// warps add it into FP32 register sums (round to nearest) while the next slab
-// fills the other buffer.  The tensor core adds into its FP32 accumulator with
-// truncation toward zero, so short per-slab accumulation (4 additions into
-// `main`, the corrections being 2^-11 smaller) bounds that bias to about
-// 2^-22 of the slab's partial sum instead of letting it grow with K; the
-// round-to-nearest sums over slabs add an unbiased 2^-24 per slab.
+// x 128 columns.  Every chunk of TC_CHUNK K slabs is accumulated afresh in one
+// buffer; the drain warps add it into FP32 register sums (round to nearest)
+// while the next chunk fills the other buffer.  The tensor core adds into its
+// FP32 accumulator with truncation toward zero, so short per-chunk accumulation
+// (8 additions into `main`, the corrections being 2^-11 smaller) bounds that
+// bias to a few 2^-24 of the chunk's partial sum instead of letting it grow with
+// K; the round-to-nearest sums over chunks add an unbiased 2^-24 per chunk.
 constexpr int TC_DRAIN_WARPS = 8;
+constexpr int TC_CHUNK = 2;   // K slabs accumulated in tensor memory between drains
 constexpr int TC_THREADS_V2 = 64 + 32 * TC_DRAIN_WARPS;
 constexpr int TC_TMEM_COLS = 512;
 
@@ -195,11 +196,10 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
                    int nk_total, int slabs_per_split, double* __restrict__ C, double* __restrict__ W,
                    long long Wm, long long Wn, int* status) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int issued_parity[TC_STAGES];
-  __shared__ int mma_issued;
   __shared__ long long offCm[TC_BM], offCn[TC_BN];
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], TC_DRAIN_WARPS);
     }
+    mbar_init(&done_bar, 1);
     abort_flag = 0;
-    mma_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -269,11 +269,13 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
+      // MMA issuer: chunk ch = s / TC_CHUNK accumulates afresh in buffer ch & 1
       for (int s = 0; s < nk; ++s) {
-        const int st = s % TC_STAGES, buf = s & 1;
+        const int st = s % TC_STAGES, ch = s / TC_CHUNK, buf = ch & 1;
+        const bool first = (s % TC_CHUNK) == 0;
+        const bool last = (s % TC_CHUNK) == TC_CHUNK - 1 || s == nk - 1;
         if (!mbar_wait(&full[st], (s / TC_STAGES) & 1, ab)) break;
-        if (s >= 2 && !mbar_wait(&acc_empty[buf], ((s >> 1) - 1) & 1, ab)) break;
+        if (first && ch >= 2 && !mbar_wait(&acc_empty[buf], ((ch >> 1) - 1) & 1, ab)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dmain = tmem + (uint32_t)(buf * 256), dcorr = dmain + 128;
         const uint32_t sa = smem_addr(base + st * TC_STAGE);
@@ -282,13 +284,18 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 8; ++kk) {
           const uint64_t adv = (uint64_t)(kk * 8 * 4) >> 4;   // 8 TF32 values = 32 bytes along K
-          mma_tf32(dmain, ahi + adv, bhi + adv, kk ? 1u : 0u);
-          mma_tf32(dcorr, ahi + adv, blo + adv, kk ? 1u : 0u);
+          const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
+          mma_tf32(dmain, ahi + adv, bhi + adv, acc0);
+          mma_tf32(dcorr, ahi + adv, blo + adv, acc0);
           mma_tf32(dcorr, alo + adv, bhi + adv, 1u);
         }
-        mma_commit(&empty[st]);      // slab's shared memory free once these MMAs complete
-        mma_commit(&acc_full[buf]);  // slab's partial sums ready
-        mma_issued = s + 1;
+        mma_commit(&empty[st]);                  // slab's shared memory free once these MMAs complete
+        if (last) mma_commit(&acc_full[buf]);    // chunk's partial sums ready
+      }
+      // tracks every MMA issued (normal end or abort); waited before tensor memory is freed
+      mma_commit(&done_bar);
+      const unsigned long long t0 = global_ns();
+      while (!mbar_test(&done_bar, 0) && global_ns() - t0 < TC_WAIT_NS) {
       }
     }
     __syncwarp();
@@ -300,9 +307,10 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0.f;
     bool ok = true;
-    for (int s = 0; s < nk; ++s) {
-      const int buf = s & 1;
-      if (!mbar_wait(&acc_full[buf], (s >> 1) & 1, ab)) {
+    const int nch = (nk + TC_CHUNK - 1) / TC_CHUNK;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      if (!mbar_wait(&acc_full[buf], (ch >> 1) & 1, ab)) {
         ok = false;
         break;
       }
@@ -360,11 +368,8 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
         while (!mbar_test(&full[st], (uint32_t)issued_parity[st]) && global_ns() - t0 < TC_WAIT_NS) {
         }
       }
-      const int s = mma_issued - 1;   // last slab whose MMAs were issued
-      if (s >= 0) {
-        const unsigned long long t0 = global_ns();
-        while (!mbar_test(&acc_full[s & 1], (s >> 1) & 1) && global_ns() - t0 < TC_WAIT_NS) {
-        }
+      const unsigned long long t0 = global_ns();
+      while (!mbar_test(&done_bar, 0) && global_ns() - t0 < TC_WAIT_NS) {
       }
     }
     __syncthreads();
