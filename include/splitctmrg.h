@@ -64,7 +64,7 @@ typedef struct {
                                columns, Cholesky-QR bases, power_steps steps) when the
                                truncated space exceeds 2 chi and randomized_min;
                                decompositions and Gram matrices in FP64; default
-                               cutoff 1e-6.
+                               cutoff 1e-5.
                             2: as 1 with every contraction on the CUDA cores (FP32).
                             3: FP64 arithmetic throughout with the randomized
                                projectors of 1 (cutoff default 1e-6). */

@@ -252,7 +252,9 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     P.mixed = (cfg->precision >= 1);   // randomized projectors for large truncated spaces
     h->c.fp32_compute = (cfg->precision == 1 || cfg->precision == 2);
     h->c.tensor_cores = (cfg->precision == 1);
-    if (P.mixed) P.cutoff = 1e-6;   // FP32 contractions: singular values below ~1e-7 s_max are rounding noise
+    // FP32-level contractions resolve the singular vectors of values near 1e-6 s_max
+    // only to O(0.1); from 1e-5 s_max up they are accurate enough for the gradient
+    if (P.mixed) P.cutoff = h->c.fp32_compute ? 1e-5 : 1e-6;
     if (cfg->svd_cutoff > 0) P.cutoff = cfg->svd_cutoff;
     SCTM_CHECK(cfg->power_steps >= 0 && cfg->power_steps <= 16, "power_steps must be in [0, 16]");
     if (cfg->power_steps > 0) P.power_steps = cfg->power_steps;

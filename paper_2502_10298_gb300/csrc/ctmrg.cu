@@ -41,9 +41,13 @@ static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
 // Contractions of this scope run in FP64 arithmetic even in mixed mode.
 struct Fp64Scope {
   Ctx& c;
-  bool old;
+  bool old, on = true;
   explicit Fp64Scope(Ctx& cx) : c(cx), old(cx.fp32_compute) { c.fp32_compute = false; }
-  ~Fp64Scope() { c.fp32_compute = old; }
+  void end() {
+    if (on) c.fp32_compute = old;
+    on = false;
+  }
+  ~Fp64Scope() { end(); }
 };
 
 // G = Y^T Y in FP64 with the row sum split into chunks (more CTAs for the
@@ -160,9 +164,10 @@ static constexpr double kComplementMinRel = 1e-3;
 
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l, int cg_steps) {
-  // FP64 arithmetic throughout: the complement terms divide P U_bar by s_i,
-  // and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level rounding of it,
-  // amplified by 1/s_i up to the inverse cutoff, swamps the gradient
+  // FP64 arithmetic up to M_bar's factors: the complement terms divide
+  // P U_bar by s_i, and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level
+  // rounding of it, amplified by 1/s_i up to the inverse cutoff, swamps the
+  // gradient.  The final products with rho run in the handle's precision.
   Fp64Scope f64(c);
   const int k = S.shape[0];
   const int nb = U.shape[0];
@@ -238,6 +243,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
   Tensor L1 = c.empty({nb, k});
   einsum_into(c, "ai,ij->aj", U, X, L1, 1.0, 0.0, false);
   launch_axpy(L1.numel(), 1.0, A.data, L1.data, c.stream);
+  f64.end();
   // rhoB_bar += L1 (V^T rhoT^T) + U (Z^T rhoT^T)
   if (rhoB.grad) {
     Tensor gB = no_grad(rhoB);
