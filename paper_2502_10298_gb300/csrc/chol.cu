@@ -50,6 +50,71 @@ __global__ void __launch_bounds__(kCholThreads) chol_drop_kernel(int r, double* 
   }
 }
 
+// Blocked form for r <= kPanelMaxR: the factor proceeds in panels of kPanel
+// rows kept in shared memory.  A panel is factored there (pivot, deflation and
+// row updates as above), written back, and the trailing upper triangle gets
+// one rank-kPanel update from it, so every trailing entry is read and written
+// once per panel instead of once per row.
+constexpr int kPanel = 32;
+constexpr int kPanelMaxR = 832;   // kPanel * r doubles of shared memory <= 208 KB
+constexpr int kPanelThreads = 512;
+
+__global__ void __launch_bounds__(kPanelThreads) chol_panel_kernel(int r, double* __restrict__ G, double tol_rel) {
+  extern __shared__ double P[];   // kPanel x r: P[p * r + l] = row jb + p of the factor, column l
+  __shared__ double piv_s, red[kPanelThreads / 32];
+  double* Gb = G + (long long)blockIdx.x * r * r;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // largest diagonal entry (deflation reference)
+  double m = 0.0;
+  for (int i = tid; i < r; i += nt) m = fmax(m, Gb[(long long)i * r + i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  double gmax = 0.0;
+  for (int w = 0; w < nt / 32; ++w) gmax = fmax(gmax, red[w]);
+  for (int jb = 0; jb < r; jb += kPanel) {
+    const int pw = min(kPanel, r - jb), wc = r - jb;
+    for (int e = tid; e < pw * wc; e += nt) {
+      const int p = e / wc, l = jb + e % wc;
+      P[p * r + l] = (l >= jb + p) ? Gb[(long long)(jb + p) * r + l] : 0.0;
+    }
+    __syncthreads();
+    for (int p = 0; p < pw; ++p) {
+      const int j = jb + p;
+      if (tid == 0) {
+        const double d = P[p * r + j];
+        piv_s = (gmax > 0.0 && d > tol_rel * gmax) ? sqrt(d) : 0.0;
+        P[p * r + j] = piv_s;
+      }
+      __syncthreads();
+      const double piv = piv_s;
+      for (int l = j + 1 + tid; l < r; l += nt) P[p * r + l] = piv > 0.0 ? P[p * r + l] / piv : 0.0;
+      __syncthreads();
+      const int wr = r - j - 1, rows = pw - p - 1;
+      if (piv > 0.0)
+        for (int e = tid; e < rows * wr; e += nt) {
+          const int q = p + 1 + e / wr, l = j + 1 + e % wr;
+          if (l >= jb + q) P[q * r + l] -= P[p * r + jb + q] * P[p * r + l];
+        }
+      __syncthreads();
+    }
+    for (int e = tid; e < pw * wc; e += nt) {
+      const int p = e / wc, l = jb + e % wc;
+      if (l >= jb + p) Gb[(long long)(jb + p) * r + l] = P[p * r + l];
+    }
+    // trailing update: G[i][l] -= sum_p R[jb+p][i] R[jb+p][l], jb + pw <= i <= l
+    const int t0 = jb + pw, w = r - t0;
+    for (long long e = tid; e < (long long)w * w; e += nt) {
+      const int i = t0 + (int)(e / w), l = t0 + (int)(e % w);
+      if (l < i) continue;
+      double acc = 0.0;
+      for (int p = 0; p < pw; ++p) acc = fma(P[p * r + i], P[p * r + l], acc);
+      Gb[(long long)i * r + l] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
 // T = R^+ (upper triangular; rows/columns of zero pivots are zero).  One warp
 // per column; the column being built is kept in shared memory.
 constexpr int kTriWarps = 8;
@@ -89,7 +154,17 @@ void launch_chol_qr_factor(int r, int batch, double* G, double* T, double tol_re
   ProfTag profile_label(prof_enabled() ? tag : nullptr);
   {
     ProfScope ps(PF_SVD, s, (double)batch * r * (double)r * r / 3.0, (double)batch * 16.0 * r * r);
-    chol_drop_kernel<<<batch, kCholThreads, 0, s>>>(r, G, tol_rel);
+    if (r <= kPanelMaxR) {
+      const size_t psm = (size_t)kPanel * r * sizeof(double);
+      static size_t attr = 0;
+      if (psm > 48 * 1024 && psm > attr) {
+        SCTM_CUDA(cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        attr = psm;
+      }
+      chol_panel_kernel<<<batch, kPanelThreads, psm, s>>>(r, G, tol_rel);
+    } else {
+      chol_drop_kernel<<<batch, kCholThreads, 0, s>>>(r, G, tol_rel);
+    }
     SCTM_CUDA(cudaGetLastError());
   }
   ProfScope ps(PF_SVD, s, (double)batch * r * (double)r * r / 3.0, (double)batch * 16.0 * r * r);
