@@ -28,6 +28,7 @@ import ipeps_inputs as I  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe's nominal figure)
+TC_CORNER_DRAM_BYTES = 6.576915e9 + 0.52181376e9   # ncu, tc_gemm_kernel on one 8192^3 product
 
 
 def load_peaks():
@@ -278,7 +279,11 @@ def main():
         bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         peak = bf16 * 1.1 / 2.25
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tc_gemm_kernel (3xTF32 tcgen05 contraction)",
+                # DRAM bytes (read + write) of one 8192^3 enlarged-corner product, the kernel's
+                # dominant launch shape, from one ncu capture of the current kernel
+                "traffic": TC_CORNER_DRAM_BYTES,
+                "traffic_launch": "8192^3 corner product (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "kernel": "tc_gemm_kernel (3xTF32 tcgen05 contraction)",
                 "peak_source": f"TF32 = {src} bf16 sustained x 1.1/2.25 (nominal ratio)",
                 "tensor_pipe_frac": 3.0 * achieved / peak}
     else:
