@@ -31,8 +31,8 @@ static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
   for (int i = 0; i < nb; ++i) copy_into(c, Ms[i], Mb.sub(0, i));
   size_t wn = svd_work_doubles(n, n, nb);
   double* work = wn ? c.arena.alloc((long long)wn) : nullptr;
-  // Gram eigen-solves of the randomized path: eigenvalues below 1e-14 lambda_max
-  // are discarded, so their (noise-level) columns need not converge
+  // small factors of the randomized path: singular values at rounding level are
+  // discarded afterwards, so their (noise-level) columns need not converge
   launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 2.0e-29);
   for (int i = 0; i < nb; ++i) out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};
   return out;
@@ -50,19 +50,11 @@ struct Fp64Scope {
   ~Fp64Scope() { end(); }
 };
 
-// G = Y^T Y in FP64 with the row sum split into chunks (more CTAs for the
-// short, wide Gram products), then reduced.
+// G = Y^T Y in FP64.
 static Tensor gram64(Ctx& c, const Tensor& Y) {
+  // r x r output with a long row sum: the contraction splits K over extra CTAs
   Fp64Scope f(c);
-  const int m = Y.shape[0], r = Y.shape[1];
-  int sp = 16;
-  while (sp > 1 && m % sp) --sp;
-  if (sp == 1 || !Y.contiguous()) return einsum(c, "ai,aj->ij", Y, Y);
-  Tensor Y3 = Y.reshape({sp, m / sp, r});
-  Tensor Gs = einsum(c, "sai,saj->sij", Y3, Y3);
-  Tensor ones = c.empty({sp});
-  launch_fill(sp, 1.0, ones.data, c.stream);
-  return einsum(c, "sij,s->ij", Gs, ones);
+  return einsum(c, "ai,aj->ij", Y, Y);
 }
 
 // Orthonormal (or zero) columns spanning the columns of each Y_i (m_i x r):
