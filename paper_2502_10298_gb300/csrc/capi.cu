@@ -202,6 +202,7 @@ double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed
   for (int x = 0; x < h->P.Lx; ++x)
     for (int y = 0; y < h->P.Ly; ++y) {
       size_t mk = c.arena.mark();
+      const size_t tm = c.tape.mark();
       std::vector<EnergyTerm> terms = energy_patch(c, h->P, h->cell, ops, x, y);
       std::vector<double> nums(terms.size()), dens(terms.size());
       for (size_t i = 0; i < terms.size(); ++i) {
@@ -227,7 +228,7 @@ double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed
         for (size_t i = 0; i < acc.size(); ++i) hostv[i] = acc[i].second;
         for (size_t i = 0; i < acc.size(); ++i)
           SCTM_CUDA(cudaMemcpyAsync(acc[i].first, &hostv[i], sizeof(double), cudaMemcpyHostToDevice, c.stream));
-        c.tape.backward();
+        c.tape.backward_from(tm);
         SCTM_CUDA(cudaStreamSynchronize(c.stream));   // hostv must outlive the copies
       }
       c.arena.release(mk);
@@ -405,14 +406,17 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
     const int nmoves = 4 * sweeps;
     double* ck = c.arena.alloc(nE * (nmoves + 1));
     double* gbuf = c.arena.alloc(nE);
-    size_t top = c.arena.mark();
-    // forward: init + moves, untaped
-    c.tape.active = false;
-    bind_A(h, false);
+    // forward: the initial environment taped once (its tape segment and
+    // intermediates are kept and reversed last), then the moves untaped
+    bind_A(h, true);
+    c.tape.active = true;
+    const size_t init_mark = c.tape.mark();
     init_env(c, P, h->cell);
+    std::vector<SiteEnv> init_out = h->cell.env;
+    c.tape.active = false;
     save_env(h, ck);
     bind_store(h, ck);
-    c.arena.release(top);
+    size_t top = c.arena.mark();
     for (int mv = 0; mv < nmoves; ++mv) {
       move(c, P, h->cell, mv % 4);
       save_env(h, ck + (mv + 1) * nE);
@@ -421,7 +425,6 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
     }
     check_svd(h);
     // energy on the final environment, taped patch by patch
-    bind_A(h, true);
     c.tape.active = true;
     bind_leaves(h, ck + nmoves * nE);
     *e_per_site = energy_value(h, h_nn_host, h_diag_host, true);
@@ -433,19 +436,19 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
       c.tape.active = true;
       bind_leaves(h, ck + mv * nE);
       std::vector<SiteEnv> leaves = h->cell.env;
+      const size_t tm = c.tape.mark();
       move(c, P, h->cell, mv % 4);
       seed_env_grad(h, gbuf);
-      c.tape.backward();
+      c.tape.backward_from(tm);
       h->cell.env = leaves;
       read_env_grad(h, gbuf);
       c.tape.active = false;
       c.arena.release(top);
     }
-    // reverse through the initial environment
-    c.tape.active = true;
-    init_env(c, P, h->cell);
+    // reverse through the initial environment (recorded in the forward)
+    h->cell.env = init_out;
     seed_env_grad(h, gbuf);
-    c.tape.backward();
+    c.tape.backward_from(init_mark);
     c.tape.active = false;
     check_svd(h);
     SCTM_CUDA(cudaMemcpyAsync(grad_dev, h->Agrad, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));

@@ -91,9 +91,12 @@ struct Tape {
   void push(std::function<void()> f) {
     if (active) ops.push_back(std::move(f));
   }
-  void backward() {
-    for (auto it = ops.rbegin(); it != ops.rend(); ++it) (*it)();
-    ops.clear();
+  void backward() { backward_from(0); }
+  // run (in reverse) and drop only the closures recorded after mark()
+  size_t mark() const { return ops.size(); }
+  void backward_from(size_t m) {
+    for (size_t i = ops.size(); i > m; --i) ops[i - 1]();
+    ops.resize(m);
   }
 };
 
