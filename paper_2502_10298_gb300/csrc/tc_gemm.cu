@@ -126,45 +126,37 @@ struct PackDesc {
   int k_inner;                 // 1 when the operand is contiguous along k
 };
 
-// One block: 32 rows x 128 k of the panel (four 32 x 32 tiles sharing the row
-// offsets), staged through shared memory so reads and writes are coalesced.
-constexpr int kPackK = 128;
 __global__ void __launch_bounds__(256) pack_tf32x2_kernel(PackDesc p, const double* __restrict__ X,
                                                           float* __restrict__ out) {
-  __shared__ long long offR[32], offK[kPackK];
+  __shared__ long long offR[32], offK[32];
   __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const long long k0 = (long long)blockIdx.x * kPackK, r0 = (long long)blockIdx.y * 32, b = blockIdx.z;
+  const long long k0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32, b = blockIdx.z;
   if (tid < 32) {
     long long r = r0 + tid;
     offR[tid] = r < p.R ? group_offset(p.rows, p.rows.sa, r) : -1;
-  } else if (tid < 32 + kPackK) {
+  } else if (tid < 64) {
     long long k = k0 + tid - 32;
     offK[tid - 32] = k < p.K ? group_offset(p.k, p.k.sa, k) : -1;
   }
   const long long ob = group_offset(p.bat, p.bat.sa, b);
-  const long long plane = p.nb * p.Rp * p.Kp;
   __syncthreads();
-  for (int kt = 0; kt < kPackK / 32; ++kt) {
-    const long long kb = k0 + kt * 32;
-    if (kb >= p.Kp) break;
-    for (int i = ty; i < 32; i += 8) {
-      // k_inner: lanes walk k (contiguous); otherwise lanes walk rows
-      int rr = p.k_inner ? i : tx, kk = p.k_inner ? tx : i;
-      long long orr = offR[rr], ok = offK[kt * 32 + kk];
-      tile[rr][kk] = (orr >= 0 && ok >= 0) ? X[ob + orr + ok] : 0.0;
-    }
-    __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-      double v = tile[i][tx];
-      uint32_t hi, lo;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"((float)v));
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"((float)(v - (double)__uint_as_float(hi))));
-      long long o = (b * p.Rp + r0 + i) * p.Kp + kb + tx;
-      out[o] = __uint_as_float(hi);
-      out[plane + o] = __uint_as_float(lo);
-    }
-    __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    // k_inner: lanes walk k (contiguous); otherwise lanes walk rows
+    int rr = p.k_inner ? i : tx, kk = p.k_inner ? tx : i;
+    long long orr = offR[rr], ok = offK[kk];
+    tile[rr][kk] = (orr >= 0 && ok >= 0) ? X[ob + orr + ok] : 0.0;
+  }
+  __syncthreads();
+  const long long plane = p.nb * p.Rp * p.Kp;
+  for (int i = ty; i < 32; i += 8) {
+    double v = tile[i][tx];
+    uint32_t hi, lo;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"((float)v));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"((float)(v - (double)__uint_as_float(hi))));
+    long long o = (b * p.Rp + r0 + i) * p.Kp + k0 + tx;
+    out[o] = __uint_as_float(hi);
+    out[plane + o] = __uint_as_float(lo);
   }
 }
 
@@ -470,14 +462,12 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
   // packing is a gather: reads the FP64 operand once, writes its hi and lo panels
   {
     ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.M * d.K + 8.0 * d.B * Kp * Mp);
-    pack_tf32x2_kernel<<<dim3((unsigned)((Kp + kPackK - 1) / kPackK), (unsigned)(Mp / 32), (unsigned)d.B), dim3(32, 8), 0,
-                         s>>>(pA, A, pa);
+    pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pA, A, pa);
     SCTM_CUDA(cudaGetLastError());
   }
   {
     ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.N * d.K + 8.0 * d.B * Kp * Np);
-    pack_tf32x2_kernel<<<dim3((unsigned)((Kp + kPackK - 1) / kPackK), (unsigned)(Np / 32), (unsigned)d.B), dim3(32, 8), 0,
-                         s>>>(pB, B, pb);
+    pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pB, B, pb);
     SCTM_CUDA(cudaGetLastError());
   }
   CUtensorMap mA = panel_map(pa, d.B, Mp, Kp, TC_BM);
