@@ -33,7 +33,9 @@ static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
   double* work = wn ? c.arena.alloc((long long)wn) : nullptr;
   // small factors of the randomized path: singular values at rounding level are
   // discarded afterwards, so their (noise-level) columns need not converge
-  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 2.0e-29);
+  // the factors come from mixed-precision products (rounding about 1e-7), so
+  // orthogonality to 1e-11 is ample
+  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 2.0e-29, 1e-11);
   for (int i = 0; i < nb; ++i) out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};
   return out;
 }

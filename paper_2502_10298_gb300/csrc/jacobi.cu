@@ -311,7 +311,7 @@ svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* _
 static bool fits_smem(int m, int n) { return (long long)(m + n) * n * 8 <= 40 * 1024; }
 
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V, double* work,
-                int* status, cudaStream_t s, double noise_rel) {
+                int* status, cudaStream_t s, double noise_rel, double tol_rel) {
   if (batch == 0 || n == 0) return;
   SCTM_CHECK(m >= n, "svd expects rows >= columns");
   char tag[96] = {0};
@@ -319,7 +319,7 @@ void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, 
     std::snprintf(tag, sizeof(tag), "jacobi m%d n%d batch%d%s", m, n, batch, fits_smem(m, n) ? " smem" : " coop");
   ProfTag profile_label(prof_enabled() ? tag : nullptr);
   const int max_sweeps = 60;
-  const double tol = 2.3e-16 * 4.0 * sqrt((double)m);
+  const double tol = tol_rel > 0.0 ? tol_rel : 2.3e-16 * 4.0 * sqrt((double)m);
   const int in_smem = fits_smem(m, n);
   size_t smem = in_smem ? (size_t)(m + n) * n * sizeof(double) : 0;
   if (!in_smem) {

@@ -33,8 +33,10 @@ void launch_gaussian(long long rows, long long cols, unsigned long long seed, do
 // noise_rel > 0: a column pair in which either column has norm^2 below
 // noise_rel ||M||_F^2 still rotates but never keeps the sweep loop going (for
 // decompositions whose noise-level directions are discarded afterwards).
+// tol_rel > 0 replaces the default orthogonality threshold |w_i.w_j| <= tol |w_i||w_j|
+// (4 eps sqrt(m)) for decompositions that need less.
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V,
-                double* work, int* status, cudaStream_t s, double noise_rel = 0.0);
+                double* work, int* status, cudaStream_t s, double noise_rel = 0.0, double tol_rel = 0.0);
 size_t svd_work_doubles(int m, int n, int batch);
 
 // out[g] = alpha * in[g] + beta * out[g] over one index group g (strides sa = in, sc = out).

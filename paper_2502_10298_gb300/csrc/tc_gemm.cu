@@ -415,8 +415,10 @@ long long round_up(long long v, long long q) { return (v + q - 1) / q * q; }
 }  // namespace
 
 bool tc_eligible(const ContractDesc& d) {
-  // worth a tile of 128 x 128 and representable by the tensor maps
-  return d.M >= 64 && d.N >= 64 && d.K >= 32 && d.B <= 65535 &&
+  // worth a tile of 128 x 128 and representable by the tensor maps; below 128
+  // of K (four slabs) the per-tile set-up and epilogue outweigh the MMAs, and
+  // the CUDA-core kernel is faster
+  return d.M >= 64 && d.N >= 64 && d.K >= 128 && d.B <= 65535 &&
          2.0 * d.B * d.M * d.N * d.K >= 1e8 && round_up(d.M, TC_BM) / TC_BM * (round_up(d.N, TC_BN) / TC_BN) < (1LL << 31);
 }
 
