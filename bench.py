@@ -187,6 +187,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--algorithm", default="split", choices=["split", "conventional"],
+                    help="split CTMRG (the method) or the conventional double-layer CTMRG it is compared with")
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
                     help="time one kernel alone instead of the evaluation (profiling aid)")
     ap.add_argument("--workspace-gb", type=float, default=None)
@@ -213,8 +215,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     stream = torch.cuda.current_stream()
     prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
+    algo = 1 if args.algorithm == "conventional" else 0
     s = S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec,
-                     workspace_bytes=args_ws(c, args.workspace_gb))
+                     workspace_bytes=args_ws(c, args.workspace_gb), algorithm=algo)
+    if algo:
+        desc = desc + ", conventional double-layer CTMRG"
 
     def step():
         return s.energy_grad(At, sweeps, h_nn, h_diag)

@@ -84,6 +84,12 @@ typedef struct {
                             2 chi computed triplets coupled exactly; n > 0 = only the
                             first chi + n - 1 (the rest of the spectrum is treated
                             as the complement)                                      */
+  int algorithm;         /* 0: split CTMRG (Sec. II.B).  1: the conventional double-
+                            layer CTMRG the paper compares against (Sec. III), with
+                            2x2-patch projectors; its edges are the fused ket-bra pairs
+                            [previous, ket leg, bra leg, next] (chi x D x D x chi) and
+                            the same calls (init, move, energy_2x2, energy_grad) apply;
+                            ctmrg_projectors is not available for it                */
 } sctm_config;
 
 /* Create a handle.  stream: a cudaStream_t (NULL = legacy default stream). */
@@ -135,7 +141,8 @@ SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int swee
                      const double* h_diag_host, double* e_per_site, double* grad_host);
 
 /* Environment of site (x, y) into out_dev, packed in the order C1 T1k T1b C2
- * T2k T2b C3 T3b T3k C4 T4b T4k (chi^2 or chi*D*chi doubles each). */
+ * T2k T2b C3 T3b T3k C4 T4b T4k (chi^2 or chi*D*chi doubles each); for the
+ * conventional algorithm C1 T1 C2 T2 C3 T3 C4 T4 (chi^2 or chi*D*D*chi each). */
 SCTM_API int sctm_get_env(sctm_handle h, int x, int y, double* out_dev);
 
 /* Singular value decomposition M = U diag(S) V^T of an m x n row-major

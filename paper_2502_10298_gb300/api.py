@@ -16,6 +16,7 @@ __all__ = [
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsplitctmrg.so")
 ENV_KEYS = ("C1", "T1k", "T1b", "C2", "T2k", "T2b", "C3", "T3b", "T3k", "C4", "T4b", "T4k")
+CONV_KEYS = ("C1", "T1", "C2", "T2", "C3", "T3", "C4", "T4")
 _ERRORS = {-1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_SVD_NOCONV", -4: "ERR_NONFINITE", -5: "ERR_OOM",
            -6: "ERR_STATE"}
 
@@ -31,7 +32,7 @@ class Config(ctypes.Structure):
                 ("chi", ctypes.c_int), ("precision", ctypes.c_int), ("svd_cutoff", ctypes.c_double),
                 ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("power_steps", ctypes.c_int), ("randomized_min", ctypes.c_int),
-                ("adjoint_cg_steps", ctypes.c_int), ("adjoint_band", ctypes.c_int)]
+                ("adjoint_cg_steps", ctypes.c_int), ("adjoint_band", ctypes.c_int), ("algorithm", ctypes.c_int)]
 
 
 _lib = None
@@ -88,10 +89,10 @@ def _hp(a):
 
 
 def sctm_create(Lx, Ly, p, D, chi, precision=0, svd_cutoff=0.0, lorentz_eps=0.0, workspace_bytes=0,
-                stream=None, power_steps=0, randomized_min=0, adjoint_cg_steps=0, adjoint_band=0):
+                stream=None, power_steps=0, randomized_min=0, adjoint_cg_steps=0, adjoint_band=0, algorithm=0):
     lib = load_library()
     cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes, power_steps,
-                 randomized_min, adjoint_cg_steps, adjoint_band)
+                 randomized_min, adjoint_cg_steps, adjoint_band, algorithm)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     h = ctypes.c_void_p()
@@ -159,14 +160,20 @@ def energy_grad_host(h, A_cell: np.ndarray, sweeps: int, h_nn, h_diag=None, grad
     return e.value, grad_out
 
 
-def sctm_get_env(h, x, y, chi, D):
-    sizes = [chi * chi if k[0] == "C" else chi * D * chi for k in ENV_KEYS]
+def sctm_get_env(h, x, y, chi, D, conventional=False):
+    """Environment of site (x, y): split keys (C1, T1k, T1b, ...) or, for the
+    conventional algorithm, C1, T1, C2, T2, C3, T3, C4, T4 with fused edges."""
+    keys = CONV_KEYS if conventional else ENV_KEYS
+    def shape(k):
+        if k[0] == "C":
+            return (chi, chi)
+        return (chi, D, D, chi) if conventional else (chi, D, chi)
+    sizes = [int(np.prod(shape(k))) for k in keys]
     buf = torch.empty(sum(sizes), dtype=torch.float64, device="cuda")
     _check(h, _lib.sctm_get_env(h, x, y, _dev(buf)))
     out, off = {}, 0
-    for k, n in zip(ENV_KEYS, sizes):
-        shape = (chi, chi) if k[0] == "C" else (chi, D, chi)
-        out[k] = buf[off:off + n].view(shape)
+    for k, n in zip(keys, sizes):
+        out[k] = buf[off:off + n].view(shape(k))
         off += n
     return out
 
@@ -243,6 +250,7 @@ class SplitCTMRG:
 
     def __init__(self, Lx, Ly, p, D, chi, **kw):
         self.Lx, self.Ly, self.p, self.D, self.chi = Lx, Ly, p, D, chi
+        self.conventional = kw.get("algorithm", 0) == 1
         self.h = sctm_create(Lx, Ly, p, D, chi, **kw)
 
     def close(self):
@@ -272,7 +280,7 @@ class SplitCTMRG:
         split_ctmrg_sweeps(self.h, n)
 
     def env(self, x, y):
-        return sctm_get_env(self.h, x, y, self.chi, self.D)
+        return sctm_get_env(self.h, x, y, self.chi, self.D, self.conventional)
 
     def energy(self, h_nn, h_diag=None):
         return energy_2x2(self.h, h_nn, h_diag)

@@ -21,7 +21,7 @@ struct sctm_ctx {
   double* store = nullptr;       // environment of every site
   long long env_site = 0;        // doubles per site
   long long key_off[NKEY] = {0};
-  int key_shape[NKEY][3] = {{0}};
+  int key_shape[NKEY][4] = {{0}};
   int key_nd[NKEY] = {0};
   Cell cell;
   ~sctm_ctx() {
@@ -118,10 +118,20 @@ void bind_store(sctm_handle h, double* base) {
 }
 
 // leaves for a taped region: arena copies of `base` with zeroed gradients
+// the second key of each edge pair aliases the first in a conventional environment
+bool alias_key(sctm_handle h, int k) {
+  return h->P.conventional && (k == T1b || k == T2b || k == T3k || k == T4k);
+}
+int alias_of(int k) { return k - 1; }   // pairs (T1k,T1b) (T2k,T2b) (T3b,T3k) (T4b,T4k) are adjacent
+
 void bind_leaves(sctm_handle h, double* base) {
   for (int x = 0; x < h->P.Lx; ++x)
     for (int y = 0; y < h->P.Ly; ++y)
       for (int k = 0; k < NKEY; ++k) {
+        if (alias_key(h, k)) {   // one leaf (one gradient buffer) for both slots
+          h->cell.e(x, y)[k] = h->cell.e(x, y)[alias_of(k)];
+          continue;
+        }
         Tensor src = key_view(h, base, x, y, k);
         Tensor t = h->c.empty_shape(src.shape, src.nd);   // tape active -> zeroed grad
         bool a = h->c.tape.active;
@@ -266,14 +276,26 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     P.adjoint_band = cfg->adjoint_band > 0 ? cfg->adjoint_band - 1 : -1;
     if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
     h->c.stream = (cudaStream_t)stream;
+    SCTM_CHECK(cfg->algorithm == 0 || cfg->algorithm == 1, "algorithm must be 0 (split) or 1 (conventional)");
+    P.conventional = (cfg->algorithm == 1);
     const int chi = P.chi, D = P.D;
     long long off = 0;
     for (int k = 0; k < NKEY; ++k) {
       bool corner = (k == C1 || k == C2 || k == C3 || k == C4);
+      if (alias_key(h.get(), k)) {   // conventional: same storage as the pair's first key
+        h->key_off[k] = h->key_off[alias_of(k)];
+        h->key_nd[k] = h->key_nd[alias_of(k)];
+        for (int i = 0; i < 4; ++i) h->key_shape[k][i] = h->key_shape[alias_of(k)][i];
+        continue;
+      }
       h->key_off[k] = off;
       if (corner) {
         h->key_nd[k] = 2, h->key_shape[k][0] = chi, h->key_shape[k][1] = chi;
         off += (long long)chi * chi;
+      } else if (P.conventional) {
+        h->key_nd[k] = 4, h->key_shape[k][0] = chi, h->key_shape[k][1] = D, h->key_shape[k][2] = D;
+        h->key_shape[k][3] = chi;
+        off += (long long)chi * D * D * chi;
       } else {
         h->key_nd[k] = 3, h->key_shape[k][0] = chi, h->key_shape[k][1] = D, h->key_shape[k][2] = chi;
         off += (long long)chi * D * chi;
@@ -353,6 +375,7 @@ int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P
                      double* s_host) {
   return guard(h, [&]() {
     SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
+    SCTM_CHECK(!h->P.conventional, "projector colours belong to the split scheme");
     SCTM_CHECK(dir >= 0 && dir < 4 && colour >= 0 && colour < 4, "bad dir or colour");
     size_t mk = h->c.arena.mark();
     Cell fr;

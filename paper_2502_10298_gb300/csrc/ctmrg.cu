@@ -657,25 +657,32 @@ void left_move(Ctx& c, const Params& P, Cell& cell) {
   }
 }
 
+static void any_left_move(Ctx& c, const Params& P, Cell& cell) {
+  if (P.conventional)
+    conv_left_move(c, P, cell);
+  else
+    left_move(c, P, cell);
+}
+
 void move(Ctx& c, const Params& P, Cell& cell, int dir) {
   if (dir == 0) {
-    left_move(c, P, cell);
+    any_left_move(c, P, cell);
   } else if (dir == 1) {
     Cell t = frame_transpose(cell);
     Params q = P;
     std::swap(q.Lx, q.Ly);
-    left_move(c, q, t);
+    any_left_move(c, q, t);
     cell.env = frame_transpose(t).env;
   } else if (dir == 2) {
     Cell t = frame_rot180(cell);
-    left_move(c, P, t);
+    any_left_move(c, P, t);
     cell.env = frame_rot180(t).env;
   } else if (dir == 3) {
     Cell t = frame_rot180(cell);
     Cell u = frame_transpose(t);
     Params q = P;
     std::swap(q.Lx, q.Ly);
-    left_move(c, q, u);
+    any_left_move(c, q, u);
     t.env = frame_transpose(u).env;
     cell.env = frame_rot180(t).env;
   } else {
@@ -713,6 +720,10 @@ static void split_edge_from(Ctx& c, const Params& P, const Tensor& T, const SVDR
 }
 
 void init_env(Ctx& c, const Params& P, Cell& cell) {
+  if (P.conventional) {
+    conv_init_env(c, P, cell);
+    return;
+  }
   const int D = P.D, D2 = D * D, chi = P.chi;
   SCTM_CHECK(D2 <= chi, "chi must be at least D^2 (initial corner dimension)");
   struct Pieces { Tensor c1, t1, c2, t2, c3, t3, c4, t4; };
@@ -946,14 +957,18 @@ std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const 
       SiteEnv& eTR = cell.e(x, y + 1);
       SiteEnv& eBR = cell.e(x + 1, y + 1);
       SiteEnv& eBL = cell.e(x + 1, y);
-      Tensor T1L = fuse_edge(c, eTL[T1k], eTL[T1b], "aui,iwc->auwc");
-      Tensor T4T = fuse_edge(c, eTL[T4b], eTL[T4k], "nvq,qlb->nvlb");
-      Tensor T1R = fuse_edge(c, eTR[T1k], eTR[T1b], "aui,iwc->auwc");
-      Tensor T2T = fuse_edge(c, eTR[T2k], eTR[T2b], "frj,jzg->frzg");
-      Tensor T2B = fuse_edge(c, eBR[T2k], eBR[T2b], "frj,jzg->frzg");
-      Tensor T3R = fuse_edge(c, eBR[T3b], eBR[T3k], "hek,kdm->hedm");
-      Tensor T3L = fuse_edge(c, eBL[T3b], eBL[T3k], "hek,kdm->hedm");
-      Tensor T4B = fuse_edge(c, eBL[T4b], eBL[T4k], "nvq,qlb->nvlb");
+      // conventional environments hold the fused edges already
+      auto fused = [&](const Tensor& a, const Tensor& b, const char* spec) {
+        return P.conventional ? a : fuse_edge(c, a, b, spec);
+      };
+      Tensor T1L = fused(eTL[T1k], eTL[T1b], "aui,iwc->auwc");
+      Tensor T4T = fused(eTL[T4b], eTL[T4k], "nvq,qlb->nvlb");
+      Tensor T1R = fused(eTR[T1k], eTR[T1b], "aui,iwc->auwc");
+      Tensor T2T = fused(eTR[T2k], eTR[T2b], "frj,jzg->frzg");
+      Tensor T2B = fused(eBR[T2k], eBR[T2b], "frj,jzg->frzg");
+      Tensor T3R = fused(eBR[T3b], eBR[T3k], "hek,kdm->hedm");
+      Tensor T3L = fused(eBL[T3b], eBL[T3k], "hek,kdm->hedm");
+      Tensor T4B = fused(eBL[T4b], eBL[T4k], "nvq,qlb->nvlb");
       const Tensor& aTL = cell.a(x, y);
       const Tensor& aTR = cell.a(x, y + 1);
       const Tensor& aBR = cell.a(x + 1, y + 1);
@@ -1010,6 +1025,119 @@ std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const 
       }
     }
   return terms;
+}
+
+// ------------------------------------------------------------------ conventional CTMRG
+// The double-layer (conventional) directional CTMRG that the paper benchmarks
+// the split scheme against (Sec. III), with the 2x2-patch projectors of
+// Corboz et al.: an edge is the fused ket-bra pair [previous, ket leg, bra leg,
+// next] (the contraction of a split pair over the interlayer bond, Sec. II.B),
+// stored in both slots of its pair (T1k = T1b, T2k = T2b, T3b = T3k,
+// T4b = T4k), so the transposed and rotated frames of the split environment
+// map it unchanged.
+
+void conv_init_env(Ctx& c, const Params& P, Cell& cell) {
+  const int D = P.D, D2 = D * D, chi = P.chi;
+  SCTM_CHECK(D2 <= chi, "chi must be at least D^2 (initial corner dimension)");
+  struct Pieces { Tensor c1, t1, c2, t2, c3, t3, c4, t4; };
+  std::vector<Pieces> pc(cell.Lx * cell.Ly);
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      const Tensor& A = cell.a(x, y);
+      Pieces& q = pc[x * cell.Ly + y];
+      q.c1 = einsum(c, "suldr,sulez->rzde", A, A).reshape({D2, D2});
+      q.t1 = einsum(c, "suldr,suvez->lvderz", A, A).reshape({D2, D, D, D2});
+      q.c2 = einsum(c, "suldr,suver->lvde", A, A).reshape({D2, D2});
+      q.t2 = einsum(c, "suldr,swver->uwlvde", A, A).reshape({D2, D, D, D2});
+      q.c3 = einsum(c, "suldr,swvdr->uwlv", A, A).reshape({D2, D2});
+      q.t3 = einsum(c, "suldr,swvdz->rzwulv", A, A).reshape({D2, D, D, D2});
+      q.c4 = einsum(c, "suldr,swldz->rzuw", A, A).reshape({D2, D2});
+      q.t4 = einsum(c, "suldr,swlez->dezruw", A, A).reshape({D2, D, D, D2});
+    }
+  auto P_ = [&](int x, int y) -> Pieces& {
+    x = (x % cell.Lx + cell.Lx) % cell.Lx;
+    y = (y % cell.Ly + cell.Ly) % cell.Ly;
+    return pc[x * cell.Ly + y];
+  };
+  auto padC = [&](const Tensor& m) {
+    Tensor z = c.zeros({chi, chi});
+    Tensor v = z;
+    v.shape[0] = D2;
+    v.shape[1] = D2;
+    copy_into(c, m, v);
+    return z;
+  };
+  auto padT = [&](const Tensor& t) {
+    Tensor z = c.zeros({chi, D, D, chi});
+    Tensor v = z;
+    v.shape[0] = D2;
+    v.shape[3] = D2;
+    copy_into(c, t, v);
+    return z;
+  };
+  for (int x = 0; x < cell.Lx; ++x)
+    for (int y = 0; y < cell.Ly; ++y) {
+      SiteEnv& e = cell.e(x, y);
+      e[C1] = padC(P_(x - 1, y - 1).c1);
+      e[C2] = padC(P_(x - 1, y + 1).c2);
+      e[C3] = padC(P_(x + 1, y + 1).c3);
+      e[C4] = padC(P_(x + 1, y - 1).c4);
+      e[T1k] = e[T1b] = padT(P_(x - 1, y).t1);
+      e[T2k] = e[T2b] = padT(P_(x, y + 1).t2);
+      e[T3b] = e[T3k] = padT(P_(x + 1, y).t3);
+      e[T4b] = e[T4k] = padT(P_(x, y - 1).t4);
+    }
+}
+
+void conv_left_move(Ctx& c, const Params& P, Cell& cell) {
+  const int Lx = cell.Lx, Ly = cell.Ly, D = P.D, k = P.chi;
+  for (int y = 0; y < Ly; ++y) {
+    // projectors of the cuts below every row of column y: upper half TL^T TR,
+    // lower half BR BL^T of the 2x2 patch anchored at (x, y)
+    std::vector<Tensor> rT(Lx), rB(Lx);
+    for (int x = 0; x < Lx; ++x) {
+      SiteEnv& eTL = cell.e(x, y);
+      SiteEnv& eTR = cell.e(x, y + 1);
+      SiteEnv& eBR = cell.e(x + 1, y + 1);
+      SiteEnv& eBL = cell.e(x + 1, y);
+      const Tensor& aTL = cell.a(x, y);
+      const Tensor& aTR = cell.a(x, y + 1);
+      const Tensor& aBR = cell.a(x + 1, y + 1);
+      const Tensor& aBL = cell.a(x + 1, y);
+      Tensor TL = finish_TL(c, half_TL(c, eTL[C1], eTL[T1k], eTL[T4k], aTL), aTL);   // [(c,r,z), (n,d,e)]
+      Tensor TR = finish_TR(c, half_TR(c, eTR[T1k], eTR[C2], eTR[T2k], aTR), aTR);   // [(a,l,v), (d,e,g)]
+      Tensor BR = finish_BR(c, half_BR(c, eBR[T2k], eBR[C3], eBR[T3k], aBR), aBR);   // [(u,w,f), (l,v,m)]
+      Tensor BL = finish_BL(c, half_BL(c, eBL[T4k], eBL[C4], eBL[T3k], aBL), aBL);   // [(b,u,w), (r,z,h)]
+      rT[x] = einsum(c, "ra,rb->ab", TL, TR);   // alpha = TL's lower cut (n,d,e)  x  beta
+      rB[x] = einsum(c, "al,bl->ab", BR, BL);   // beta x alpha
+    }
+    std::vector<ProjPair> pp = projectors(c, P, rT, rB);
+    const int n = cell.e(0, y)[T4k].shape[0];
+    std::vector<std::array<Tensor, 3>> out(Lx);
+    for (int x = 0; x < Lx; ++x) {
+      SiteEnv& e = cell.e(x, y);
+      const Tensor& a = cell.a(x, y);
+      const ProjPair& pa = pp[(x + Lx - 1) % Lx];   // cut above row x
+      const ProjPair& pb = pp[x];                   // cut below row x
+      Tensor pua = pa.up.reshape({k, n, D, D}), pda = pa.dn.reshape({n, D, D, k});
+      Tensor pub = pb.up.reshape({k, n, D, D}), pdb = pb.dn.reshape({n, D, D, k});
+      Tensor X = einsum(c, "ab,auwc->buwc", e[C1], e[T1k]);
+      Tensor nC1 = einsum(c, "buwc,kbuw->ck", X, pua);
+      Tensor Z = einsum(c, "buwK,nvlb->uwKnvl", pda, e[T4k]);
+      Z = einsum(c, "uwKnvl,suldr->wKnvsdr", Z, a);
+      Z = einsum(c, "wKnvsdr,swvez->Kndrez", Z, a);
+      Tensor nT4 = einsum(c, "Kndrez,Mnde->MzrK", Z, pub);
+      Z = einsum(c, "mn,hedm->nhed", e[C4], e[T3k]);
+      Tensor nC4 = einsum(c, "nhed,ndeK->hK", Z, pdb);
+      out[x] = {rescale(c, nC1), rescale(c, nT4), rescale(c, nC4)};
+    }
+    for (int x = 0; x < Lx; ++x) {
+      SiteEnv& e = cell.e(x, y + 1);
+      e[C1] = out[x][0];
+      e[T4b] = e[T4k] = out[x][1];
+      e[C4] = out[x][2];
+    }
+  }
 }
 
 }  // namespace sctm

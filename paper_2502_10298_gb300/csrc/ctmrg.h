@@ -31,6 +31,7 @@ struct Params {
   double gram_cutoff = 1e-15; // relative cutoff on Gram eigenvalues (reduction)
   double eps_l = 1e-36;       // Lorentzian broadening (relative to s_max^4)
   bool mixed = false;         // mixed mode: FP32 contractions, randomized projectors
+  bool conventional = false;  // double-layer CTMRG (fused edges in both slots of a pair)
   int power_steps = 2;        // randomized projectors: power steps (mixed mode)
   int adjoint_cg_steps = 0;   // randomized projectors' adjoint: CG steps for the complement coupling
   int adjoint_band = -1;      // randomized projectors' adjoint: computed triplets beyond chi coupled exactly (-1: all)
@@ -67,6 +68,10 @@ void move(Ctx& c, const Params& P, Cell& cell, int dir);
 
 // environment from the neighbours' double layers, padded to chi
 void init_env(Ctx& c, const Params& P, Cell& cell);
+
+// conventional (double-layer) CTMRG: initial environment and one left move
+void conv_init_env(Ctx& c, const Params& P, Cell& cell);
+void conv_left_move(Ctx& c, const Params& P, Cell& cell);
 
 // energy pieces of one 2x2 patch: list of (numerator, denominator, weight),
 // E = sum over patches and terms of w * num / den

@@ -210,3 +210,36 @@ def test_mixed_randomized_matches_fp64_gpu(S):
     assert abs(e1 - e0) < 1e-6, (e0, e1)
     rel = float((g1 - g0).norm() / g0.norm())
     assert rel < 3e-2, rel
+
+
+@pytest.mark.parametrize("Lx,Ly,D,chi", [(1, 1, 2, 8), (2, 2, 2, 8)])
+def test_conventional_ctmrg_energy_matches_oracle(S, Lx, Ly, D, chi):
+    """Conventional double-layer CTMRG (algorithm 1) on the GPU against the
+    oracle's conv_ctmrg: energy after three sweeps to 1e-10 relative."""
+    A = _near(Lx, Ly, D, 0.3, seed=13)
+    h, hd = (HR, None) if Lx == 1 else (H, 0.5 * H)
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, algorithm=1) as s:
+        s.init(torch.tensor(A, device="cuda"))
+        s.sweeps(3)
+        e_gpu = s.energy(h, hd)
+        env = s.env(0, 0)
+        assert set(env) == {"C1", "T1", "C2", "T2", "C3", "T3", "C4", "T4"}
+    Ac = C.as_cell(A)
+    e_or = float(En.energy_per_site(Ac, C.conv_ctmrg(Ac, chi, 3), h, hd, split=False))
+    assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
+
+
+def test_conventional_ctmrg_gradient_matches_oracle(S):
+    """Gradient of the conventional CTMRG energy (two sweeps) against the
+    oracle's autograd, 1e-7 relative."""
+    Lx, Ly, D, chi, sweeps = 1, 1, 2, 8, 2
+    A = I.random_cell(Lx, Ly, 2, D, seed=3)
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, algorithm=1) as s:
+        e, g = s.energy_grad(torch.tensor(A, device="cuda"), sweeps, HR, None)
+    Ao = torch.tensor(A).requires_grad_(True)
+    Ac = [[Ao[0, 0]]]
+    eo = En.energy_per_site(Ac, C.conv_ctmrg(Ac, chi, sweeps), HR, None, split=False)
+    eo.backward()
+    assert abs(e - float(eo)) < 1e-10 * abs(float(eo))
+    rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
+    assert rel < 1e-7, rel
