@@ -189,6 +189,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--algorithm", default="split", choices=["split", "conventional"],
                     help="split CTMRG (the method) or the conventional double-layer CTMRG it is compared with")
+    ap.add_argument("--move-scaling", action="store_true",
+                    help="time one directional move of the split and the conventional CTMRG against D at "
+                         "fixed chi (the paper's Fig. 4a comparison) instead of the evaluation")
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
                     help="time one kernel alone instead of the evaluation (profiling aid)")
     ap.add_argument("--workspace-gb", type=float, default=None)
@@ -197,6 +200,8 @@ def main():
         return run_reference(args)
     if args.kernel:
         return run_kernel(args)
+    if args.move_scaling:
+        return run_move_scaling(args)
 
     import torch
     import paper_2502_10298_gb300 as S
@@ -348,6 +353,36 @@ def run_kernel(args):
                       "peak_tf32_tflops": peak, "frac": ach / peak, "tensor_pipe_frac": 3 * ach / peak,
                       "pack_ms_per_step": prof["other"]["ms"] / max(1, args.steps),
                       "peak_source": f"{src} bf16 burst x 1.1/2.25"}))
+    return 0
+
+
+def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8)):
+    """Device time of one directional move (mean over a sweep of four, after one
+    warm-up sweep) for the split and the conventional CTMRG at fixed chi, 1x1
+    cell, seeded N(0,1) tensor, mixed precision: the shape of the paper's
+    Fig. 4a (time of one absorption step against the bulk bond dimension)."""
+    import torch
+    import paper_2502_10298_gb300 as S
+    rows = []
+    for D in Ds:
+        A = I.random_cell(1, 1, 2, D, seed=0)
+        At = torch.tensor(A, device="cuda")
+        row = {"D": D, "chi": chi}
+        for name, algo in (("split", 0), ("conventional", 1)):
+            n = chi * D * D
+            ws = int(min(200 * 2**30, max(8 * 2**30, 40 * n * n * 8)))
+            with S.SplitCTMRG(1, 1, 2, D, chi, precision=1, workspace_bytes=ws, algorithm=algo) as s:
+                s.init(At)
+                s.sweeps(1)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                s.sweeps(1)
+                ev1.record()
+                torch.cuda.synchronize()
+                row[name + "_ms_per_move"] = ev0.elapsed_time(ev1) / 4
+        rows.append(row)
+        print(json.dumps(row), flush=True)
     return 0
 
 
