@@ -84,6 +84,8 @@ typedef struct {
                             2 chi computed triplets coupled exactly; n > 0 = only the
                             first chi + n - 1 (the rest of the spectrum is treated
                             as the complement)                                      */
+  int rank_extra;        /* mixed mode, randomized projectors: columns beyond chi in the
+                            sketch (0: chi, i.e. 2 chi columns)                      */
   int algorithm;         /* 0: split CTMRG (Sec. II.B).  1: the conventional double-
                             layer CTMRG the paper compares against (Sec. III), with
                             2x2-patch projectors; its edges are the fused ket-bra pairs

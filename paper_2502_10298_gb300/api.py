@@ -32,7 +32,8 @@ class Config(ctypes.Structure):
                 ("chi", ctypes.c_int), ("precision", ctypes.c_int), ("svd_cutoff", ctypes.c_double),
                 ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("power_steps", ctypes.c_int), ("randomized_min", ctypes.c_int),
-                ("adjoint_cg_steps", ctypes.c_int), ("adjoint_band", ctypes.c_int), ("algorithm", ctypes.c_int)]
+                ("adjoint_cg_steps", ctypes.c_int), ("adjoint_band", ctypes.c_int),
+                ("rank_extra", ctypes.c_int), ("algorithm", ctypes.c_int)]
 
 
 _lib = None
@@ -89,10 +90,11 @@ def _hp(a):
 
 
 def sctm_create(Lx, Ly, p, D, chi, precision=0, svd_cutoff=0.0, lorentz_eps=0.0, workspace_bytes=0,
-                stream=None, power_steps=0, randomized_min=0, adjoint_cg_steps=0, adjoint_band=0, algorithm=0):
+                stream=None, power_steps=0, randomized_min=0, adjoint_cg_steps=0, adjoint_band=0, algorithm=0,
+                rank_extra=0):
     lib = load_library()
     cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes, power_steps,
-                 randomized_min, adjoint_cg_steps, adjoint_band, algorithm)
+                 randomized_min, adjoint_cg_steps, adjoint_band, rank_extra, algorithm)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     h = ctypes.c_void_p()

@@ -270,6 +270,8 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     SCTM_CHECK(cfg->power_steps >= 0 && cfg->power_steps <= 16, "power_steps must be in [0, 16]");
     if (cfg->power_steps > 0) P.power_steps = cfg->power_steps;
     if (cfg->randomized_min > 0) P.randomized_min = cfg->randomized_min;
+    SCTM_CHECK(cfg->rank_extra >= 0, "rank_extra must be >= 0");
+    P.rank_extra = cfg->rank_extra > 0 ? cfg->rank_extra : P.chi;
     SCTM_CHECK(cfg->adjoint_cg_steps >= 0 && cfg->adjoint_cg_steps <= 64, "adjoint_cg_steps must be in [0, 64]");
     P.adjoint_cg_steps = cfg->adjoint_cg_steps;
     SCTM_CHECK(cfg->adjoint_band >= 0, "adjoint_band must be >= 0");

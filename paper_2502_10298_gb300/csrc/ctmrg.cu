@@ -312,7 +312,7 @@ static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, c
 
 static bool use_randomized(const Params& P, const Tensor& rhoT) {
   const int n = std::min(rhoT.shape[0], rhoT.shape[1]);
-  return P.mixed && n > 2 * P.chi && n >= P.randomized_min;
+  return P.mixed && n > P.chi + P.rank_extra && n >= P.randomized_min;
 }
 
 std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB) {
@@ -331,7 +331,7 @@ std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tens
   if (!ri.empty()) {
     bool tap = c.tape.active;
     c.tape.active = false;
-    std::vector<Trunc> t = randomized_svd_batch(c, bT, bB, 2 * P.chi, P.power_steps);
+    std::vector<Trunc> t = randomized_svd_batch(c, bT, bB, P.chi + P.rank_extra, P.power_steps);
     c.tape.active = tap;
     for (size_t j = 0; j < ri.size(); ++j) out[ri[j]] = finish_randomized(c, P, bT[j], bB[j], t[j]);
   }
@@ -345,7 +345,7 @@ ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rh
   if (use_randomized(P, rhoT)) {
     bool tap = c.tape.active;
     c.tape.active = false;
-    Trunc t = randomized_svd_batch(c, {rhoT}, {rhoB}, 2 * k, P.power_steps)[0];
+    Trunc t = randomized_svd_batch(c, {rhoT}, {rhoB}, k + P.rank_extra, P.power_steps)[0];
     c.tape.active = tap;
     return finish_randomized(c, P, rhoT, rhoB, t);
   }

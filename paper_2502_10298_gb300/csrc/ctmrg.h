@@ -33,6 +33,7 @@ struct Params {
   bool mixed = false;         // mixed mode: FP32 contractions, randomized projectors
   bool conventional = false;  // double-layer CTMRG (fused edges in both slots of a pair)
   int power_steps = 2;        // randomized projectors: power steps (mixed mode)
+  int rank_extra = 0;         // randomized projectors: columns beyond chi (set from chi at creation)
   int adjoint_cg_steps = 0;   // randomized projectors' adjoint: CG steps for the complement coupling
   int adjoint_band = -1;      // randomized projectors' adjoint: computed triplets beyond chi coupled exactly (-1: all)
   int randomized_min = 256;   // randomized projectors only when the truncated space has >= this dimension
