@@ -60,9 +60,9 @@ typedef struct {
                             1: mixed -- large contractions on the tcgen05 tensor cores
                                as 3xTF32 (operands split into TF32 hi + lo, FP32
                                accumulation), small ones in FP32 on the CUDA cores;
-                               projectors from a randomized subspace iteration (2 chi
-                               columns, Cholesky-QR bases, power_steps steps) when the
-                               truncated space exceeds 2 chi and randomized_min;
+                               projectors from a randomized subspace iteration (chi +
+                               rank_extra columns, Cholesky-QR bases, power_steps steps)
+                               when the truncated space exceeds that and randomized_min;
                                decompositions and Gram matrices in FP64; default
                                cutoff 1e-5.
                             2: as 1 with every contraction on the CUDA cores (FP32).
@@ -81,11 +81,11 @@ typedef struct {
                             n > 0 = n conjugate-gradient steps on the first-order
                             coupling (experimental)                                */
   int adjoint_band;      /* mixed mode, reverse pass of randomized projectors: 0 = all
-                            2 chi computed triplets coupled exactly; n > 0 = only the
+                            chi + rank_extra computed triplets coupled exactly; n > 0 = only the
                             first chi + n - 1 (the rest of the spectrum is treated
                             as the complement)                                      */
   int rank_extra;        /* mixed mode, randomized projectors: columns beyond chi in the
-                            sketch (0: chi, i.e. 2 chi columns)                      */
+                            sketch (0: max(32, chi / 2))                             */
   int algorithm;         /* 0: split CTMRG (Sec. II.B).  1: the conventional double-
                             layer CTMRG the paper compares against (Sec. III), with
                             2x2-patch projectors; its edges are the fused ket-bra pairs

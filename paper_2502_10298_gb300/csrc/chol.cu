@@ -156,10 +156,13 @@ void launch_chol_qr_factor(int r, int batch, double* G, double* T, double tol_re
     ProfScope ps(PF_SVD, s, (double)batch * r * (double)r * r / 3.0, (double)batch * 16.0 * r * r);
     if (r <= kPanelMaxR) {
       const size_t psm = (size_t)kPanel * r * sizeof(double);
-      static size_t attr = 0;
-      if (psm > 48 * 1024 && psm > attr) {
-        SCTM_CUDA(cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-        attr = psm;
+      // opt in once to the largest panel: the kernel's static shared memory
+      // comes on top of the dynamic part, so even 48 KB of panel needs it
+      static bool attr = false;
+      if (!attr) {
+        SCTM_CUDA(cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)kPanel * kPanelMaxR * sizeof(double))));
+        attr = true;
       }
       chol_panel_kernel<<<batch, kPanelThreads, psm, s>>>(r, G, tol_rel);
     } else {
@@ -170,7 +173,7 @@ void launch_chol_qr_factor(int r, int batch, double* G, double* T, double tol_re
   ProfScope ps(PF_SVD, s, (double)batch * r * (double)r * r / 3.0, (double)batch * 16.0 * r * r);
   const int cols_per_mat = (r + kTriWarps - 1) / kTriWarps;
   const size_t smem = (size_t)kTriWarps * r * sizeof(double);
-  if (smem > 48 * 1024)
+  if (smem >= 48 * 1024)
     SCTM_CUDA(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   tri_inv_kernel<<<batch * cols_per_mat, 32 * kTriWarps, smem, s>>>(r, G, T);
   SCTM_CUDA(cudaGetLastError());

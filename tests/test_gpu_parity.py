@@ -183,7 +183,7 @@ def _randomized_case():
 
 def test_randomized_projectors_fp64_match_exact(S):
     """Randomized projectors (the default for truncated spaces chi D = 256 and
-    chi p D = 512, both above 2 chi) with FP64 arithmetic (precision 3): energy
+    chi p D = 512, both above the chi + 32 sketch columns) with FP64 arithmetic (precision 3): energy
     within 1e-8 and gradient within 2e-4 of the exact-SVD FP64 path at the same
     cutoff, two sweeps."""
     D, chi, At = _randomized_case()
