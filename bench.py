@@ -155,16 +155,23 @@ def cpu_baseline(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
                       f"products of the 2x2 energy)"}
 
 
+def arm_config(desc, prec, world):
+    """The `config` of a bench line; the reference arm reports the same one."""
+    return {"workload": desc, "precision": prec, "l2": "flushed (256 MiB write) before every step",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
+    prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
     cb = cpu_baseline(args.config, c, A, h_nn, h_diag, sweeps, budget_s=args.cpu_budget)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "evals/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / cb["value"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc},
+            "data": "synthetic", "config": arm_config(desc, prec, 1),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -308,10 +315,9 @@ def main():
     launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f64", 1: "tf32x3 (f32 accumulate) + f64", 2: "f32 + f64"}[prec],
+            "vs_baseline": None, "dtype": {0: "f64", 1: "tf32x3 (f32 accumulate) + f64", 2: "f32 + f64", 3: "f64"}[prec],
             "data": "synthetic",
-            "config": {"workload": desc, "precision": prec, "l2": "flushed (256 MiB write) before every step",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": arm_config(desc, prec, world),
             "energy_per_site": e_val, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu,
             "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
