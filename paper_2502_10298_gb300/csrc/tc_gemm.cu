@@ -131,7 +131,10 @@ __global__ void __launch_bounds__(256) pack_tf32x2_kernel(PackDesc p, const doub
   __shared__ long long offR[32], offK[32];
   __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const long long k0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32, b = blockIdx.z;
+  // one flat grid dimension of 32 x 32 tiles (k fastest), the batch on y:
+  // row counts beyond 65535 tiles do not fit the y dimension
+  const long long nkt = p.Kp / 32, t = blockIdx.x;
+  const long long k0 = (t % nkt) * 32, r0 = (t / nkt) * 32, b = blockIdx.y;
   if (tid < 32) {
     long long r = r0 + tid;
     offR[tid] = r < p.R ? group_offset(p.rows, p.rows.sa, r) : -1;
@@ -418,8 +421,10 @@ bool tc_eligible(const ContractDesc& d) {
   // worth a tile of 128 x 128 and representable by the tensor maps; below 128
   // of K (four slabs) the per-tile set-up and epilogue outweigh the MMAs, and
   // the CUDA-core kernel is faster
+  const long long kt = round_up(d.K, TC_BK) / 32;   // 32 x 32 pack tiles along k
   return d.M >= 64 && d.N >= 64 && d.K >= 128 && d.B <= 65535 &&
-         2.0 * d.B * d.M * d.N * d.K >= 1e8 && round_up(d.M, TC_BM) / TC_BM * (round_up(d.N, TC_BN) / TC_BN) < (1LL << 31);
+         2.0 * d.B * d.M * d.N * d.K >= 1e8 && round_up(d.M, TC_BM) / TC_BM * (round_up(d.N, TC_BN) / TC_BN) < (1LL << 31) &&
+         kt * (round_up(std::max(d.M, d.N), TC_BM) / 32) < (1LL << 31);
 }
 
 // K splits: only when the output has too few tiles to fill the GPU; at least
@@ -464,12 +469,12 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
   // packing is a gather: reads the FP64 operand once, writes its hi and lo panels
   {
     ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.M * d.K + 8.0 * d.B * Kp * Mp);
-    pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pA, A, pa);
+    pack_tf32x2_kernel<<<dim3((unsigned)((Kp / 32) * (Mp / 32)), (unsigned)d.B), dim3(32, 8), 0, s>>>(pA, A, pa);
     SCTM_CUDA(cudaGetLastError());
   }
   {
     ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.N * d.K + 8.0 * d.B * Kp * Np);
-    pack_tf32x2_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32), (unsigned)d.B), dim3(32, 8), 0, s>>>(pB, B, pb);
+    pack_tf32x2_kernel<<<dim3((unsigned)((Kp / 32) * (Np / 32)), (unsigned)d.B), dim3(32, 8), 0, s>>>(pB, B, pb);
     SCTM_CUDA(cudaGetLastError());
   }
   CUtensorMap mA = panel_map(pa, d.B, Mp, Kp, TC_BM);
