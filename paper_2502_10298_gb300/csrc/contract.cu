@@ -150,11 +150,13 @@ void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, con
 
 namespace {
 constexpr int kCBM = 64, kCBN = 64, kCBK = 16;
-// K splits for outputs with too few 64 x 64 tiles; at least 256 of K per split
+// K splits for outputs with too few 64 x 64 tiles (Gram matrices of tall bases):
+// one K block per split at the least, because an SM retires only a few FP64
+// multiply-adds per clock and a small output must still occupy every SM
 long long contract_splits(const ContractDesc& d) {
   const long long tiles = ((d.M + kCBM - 1) / kCBM) * ((d.N + kCBN - 1) / kCBN) * d.B;
   const long long want = (2 * 148 + tiles - 1) / tiles;
-  long long sp = std::min<long long>(want, d.K / 256);
+  long long sp = std::min<long long>(want, d.K / kCBK);
   if (sp < 2 || d.B > 65535) return 1;
   return std::min<long long>(sp, 65535);
 }

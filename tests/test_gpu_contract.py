@@ -37,6 +37,7 @@ CASES = [
     ("bmk,bkn->bmn", (3, 200, 300), (3, 300, 300)),
     ("aub,bvc->auvc", (130, 6, 140), (140, 5, 150)),  # grouped m (a,u) and n (v,c)
     ("xkmy,ynk->mxn", (9, 33, 70, 11), (11, 200, 33)),  # two k dims in reversed order
+    ("ai,aj->ij", (432, 108), (432, 108)),        # Gram of a tall basis: few tiles, K split 27 ways
 ]
 
 
