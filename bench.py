@@ -161,8 +161,20 @@ def arm_config(desc, prec, world):
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
+def aggregate_over_ranks(total_ms, steps, world, dist, device):
+    """Timed milliseconds of the slowest rank (all-reduce MAX) and the whole-job
+    throughput: the units all ranks processed divided by that time."""
+    import torch
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / steps
+    return ms_per_step, world * 1000.0 / ms_per_step
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
@@ -171,7 +183,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "evals/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / cb["value"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": arm_config(desc, prec, 1),
+            "data": "synthetic", "config": arm_config(desc, prec, world),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -198,7 +210,7 @@ def main():
                     help="split CTMRG (the method) or the conventional double-layer CTMRG it is compared with")
     ap.add_argument("--move-scaling", action="store_true",
                     help="time one directional move of the split and the conventional CTMRG against D at "
-                         "fixed chi (the paper's Fig. 4a comparison) instead of the evaluation")
+                         "fixed chi (the paper's Fig. 5a comparison) instead of the evaluation")
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
                     help="time one kernel alone instead of the evaluation (profiling aid)")
     ap.add_argument("--workspace-gb", type=float, default=None)
@@ -259,11 +271,7 @@ def main():
     prof = S.sctm_profile(s.h, False)
     clocks = clk.stop()
     torch.cuda.synchronize()
-    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    value = world * 1000.0 / ms_per_step
+    ms_per_step, value = aggregate_over_ranks(total_ms, args.steps, world, dist, "cuda")
 
     # end-to-end through the host-buffer C-ABI call (H2D of A, D2H of grad + energy inside the timing)
     e2e = None
@@ -366,7 +374,7 @@ def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8)):
     """Device time of one directional move (mean over a sweep of four, after one
     warm-up sweep) for the split and the conventional CTMRG at fixed chi, 1x1
     cell, seeded N(0,1) tensor, mixed precision: the shape of the paper's
-    Fig. 4a (time of one absorption step against the bulk bond dimension)."""
+    Fig. 5a (time of one absorption step against the bulk bond dimension)."""
     import torch
     import paper_2502_10298_gb300 as S
     rows = []

@@ -198,7 +198,7 @@ def _near_product(Lx, Ly, D, eps, seed):
 
 def test_split_agrees_with_conventional():
     """Split and conventional CTMRG converge to the same energy (Sec. III,
-    Fig. 3a) on a generic correlated state; both are invariant under lattice
+    Fig. 4a) on a generic correlated state; both are invariant under lattice
     rotation and reflection."""
     A0 = _near_product(1, 1, 2, 0.25, seed=5)
     vals = []
@@ -207,6 +207,22 @@ def test_split_agrees_with_conventional():
         vals.append(float(En.energy_per_site(A, C.split_ctmrg(A, 12, 20), HR)))
         vals.append(float(En.energy_per_site(A, C.conv_ctmrg(A, 12, 20), HR, split=False)))
     assert max(vals) - min(vals) < 5e-7
+
+
+@pytest.mark.parametrize("split", [True, False])
+def test_energy_converges_monotonically_in_chi(split):
+    """The truncation error of the energy falls monotonically as chi grows, and
+    vanishes to rounding once chi holds every singular value above the cutoff
+    (Sec. III, Fig. 4a: the energy converges in the environment bond dimension).  A
+    projector that kept the wrong singular vectors, or paired the halves of a
+    cut the wrong way, would break the monotone decrease or the final agreement."""
+    A = C.as_cell(_near_product(1, 1, 2, 0.25, seed=5))
+    run = C.split_ctmrg if split else C.conv_ctmrg
+    E = {chi: float(En.energy_per_site(A, run(A, chi, 30), HR, split=split)) for chi in (2, 4, 8, 12, 16, 20)}
+    err = [abs(E[chi] - E[20]) for chi in (2, 4, 8, 12)]
+    assert all(b < a for a, b in zip(err, err[1:])), err
+    assert err[0] > 1e-3   # chi = 2 truncates visibly
+    assert abs(E[16] - E[20]) < 1e-10
 
 
 def test_rotation_and_gauge_invariance():
