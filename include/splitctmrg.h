@@ -114,6 +114,21 @@ SCTM_API int split_ctmrg_move(sctm_handle h, int dir);
 /* n full directional steps (left, top, right, bottom) = n sweeps. */
 SCTM_API int split_ctmrg_sweeps(sctm_handle h, int n);
 
+/* Full directional steps until the environment reaches its fixed point
+ * (Sec. II.B iterates the steps until the environment converges; the paper
+ * fixes no measure, this one is the engine's reading).  After each step the
+ * singular values of every corner of every site, each divided by the largest,
+ * are compared with those before the step; delta = max over corners of the
+ * 2-norm of the difference.  Stops after the first step with delta < tol, or
+ * after max_sweeps steps.  tol <= 0 selects 1e-12 when the contractions run
+ * in FP64 (precision 0, 3) and 1e-7 when they run in FP32 (precision 1, 2).
+ * sweeps_done and last_delta (host, may be NULL) receive the steps taken and
+ * the last delta (HUGE_VAL when max_sweeps = 0); converged iff
+ * *last_delta < tol.  Both algorithms.  Errors: SCTM_ERR_ARG (no init,
+ * max_sweeps < 0), SCTM_ERR_SVD_NOCONV, SCTM_ERR_NONFINITE (a corner
+ * spectrum is not finite), SCTM_ERR_CUDA.  Synchronises the stream. */
+SCTM_API int split_ctmrg_run(sctm_handle h, int max_sweeps, double tol, int* sweeps_done, double* last_delta);
+
 /* Projector pair of one cut of the move `dir` at the current environment,
  * without moving.  colour: 0 green, 1 teal, 2 yellow, 3 red (Sec. II.B, App. A).
  * (x, y) is the site in the frame of the move (the left-move frame is the

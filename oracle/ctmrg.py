@@ -674,12 +674,55 @@ def conv_move(A, env, direction: int, chi: int):
     return in_frame(direction, lambda a, e: conv_left_move(a, e, chi), A, env, split=False)
 
 
+def conv_sweep(A, env, chi):
+    """One full step of the conventional CTMRG: left, top, right, bottom."""
+    for d in range(4):
+        env = conv_move(A, env, d, chi)
+    return env
+
+
 def conv_ctmrg(A, chi: int, sweeps: int, env=None):
     """Conventional double-layer directional CTMRG (the paper's benchmark)."""
     A = A if isinstance(A, list) else as_cell(A)
     if env is None:
         env = initial_env(A, chi, split=False)
     for _ in range(sweeps):
-        for d in range(4):
-            env = conv_move(A, env, d, chi)
+        env = conv_sweep(A, env, chi)
     return env
+
+
+# ---------------------------------------------------------- fixed point
+def corner_spectra(env, chi: int):
+    """Singular values of the four corners of every site, each divided by its
+    largest and padded with zeros to chi (the oracle's corners grow to chi)."""
+    out = []
+    for row in env:
+        for e in row:
+            for k in ("C1", "C2", "C3", "C4"):
+                s = torch.linalg.svdvals(e[k])
+                v = torch.zeros(chi, dtype=DT)
+                v[: s.numel()] = s / s[0]
+                out.append(v)
+    return out
+
+
+def ctmrg_run(A, chi: int, tol: float, max_sweeps: int, split: bool = True):
+    """Full steps until the environment reaches its fixed point (Sec. II.B says
+    only that the steps are iterated until the environment converges; the
+    measure is the reading shared with the GPU path): after each step,
+    delta = max over corners of ||s_n - s_(n-1)||_2 of the normalised corner
+    spectra (before the first step, those of the initial environment); stop at
+    the first step with delta < tol or after max_sweeps steps.
+    Returns (env, steps done, [delta after each step])."""
+    A = A if isinstance(A, list) else as_cell(A)
+    env = initial_env(A, chi, split=split)
+    prev = corner_spectra(env, chi)
+    deltas = []
+    for n in range(1, max_sweeps + 1):
+        env = split_sweep(A, env, chi) if split else conv_sweep(A, env, chi)
+        cur = corner_spectra(env, chi)
+        deltas.append(max(float(torch.linalg.vector_norm(a - b)) for a, b in zip(cur, prev)))
+        prev = cur
+        if deltas[-1] < tol:
+            return env, n, deltas
+    return env, max_sweeps, deltas

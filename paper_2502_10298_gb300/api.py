@@ -9,7 +9,7 @@ import torch
 
 __all__ = [
     "load_library", "Config", "sctm_create", "sctm_destroy", "split_ctmrg_init", "split_ctmrg_move",
-    "split_ctmrg_sweeps", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
+    "split_ctmrg_sweeps", "split_ctmrg_run", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
     "sctm_get_env", "sctm_workspace_high_water", "sctm_profile", "sctm_svd", "sctm_svd_noalloc", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
 ]
 
@@ -57,6 +57,7 @@ def load_library(path: str = LIB_PATH):
         "split_ctmrg_init": (i, [vp, vp]),
         "split_ctmrg_move": (i, [vp, i]),
         "split_ctmrg_sweeps": (i, [vp, i]),
+        "split_ctmrg_run": (i, [vp, i, d, _ip, _dp]),
         "ctmrg_projectors": (i, [vp, i, i, i, i, vp, vp, _dp]),
         "energy_2x2": (i, [vp, _dp, _dp, _dp]),
         "energy_grad": (i, [vp, vp, i, _dp, _dp, _dp, vp]),
@@ -123,6 +124,14 @@ def split_ctmrg_move(h, direction: int):
 
 def split_ctmrg_sweeps(h, n: int):
     _check(h, _lib.split_ctmrg_sweeps(h, int(n)))
+
+
+def split_ctmrg_run(h, max_sweeps: int, tol: float = 0.0):
+    """Steps until the corner spectra change by less than tol (0: the default
+    of the precision); returns (steps done, last delta)."""
+    n, dl = ctypes.c_int(), ctypes.c_double()
+    _check(h, _lib.split_ctmrg_run(h, int(max_sweeps), float(tol), ctypes.byref(n), ctypes.byref(dl)))
+    return n.value, dl.value
 
 
 def ctmrg_projectors(h, direction, x, y, colour, chi, alpha):
@@ -280,6 +289,9 @@ class SplitCTMRG:
 
     def sweeps(self, n):
         split_ctmrg_sweeps(self.h, n)
+
+    def run(self, max_sweeps, tol=0.0):
+        return split_ctmrg_run(self.h, max_sweeps, tol)
 
     def env(self, x, y):
         return sctm_get_env(self.h, x, y, self.chi, self.D, self.conventional)

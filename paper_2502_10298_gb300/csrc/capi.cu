@@ -4,6 +4,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <vector>
 
 #include "../../include/splitctmrg.h"
 #include "ctmrg.h"
@@ -193,6 +194,48 @@ void check_svd(sctm_handle h) {
   }
 }
 
+// Singular values of the four corners of every site (batched FP64 Jacobi SVD of
+// the stored chi x chi corners), each spectrum divided by its largest value:
+// host vector [site][corner][chi]; zero-padded corners give trailing zeros.
+std::vector<double> corner_spectra(sctm_handle h) {
+  const int chi = h->P.chi;
+  const int nc = h->P.Lx * h->P.Ly * 4;
+  const long long mm = (long long)chi * chi;
+  std::vector<double> out((size_t)nc * chi, 0.0);
+  size_t mk = h->c.arena.mark();
+  double* M = h->c.arena.alloc(nc * mm);
+  double* U = h->c.arena.alloc(nc * mm);
+  double* V = h->c.arena.alloc(nc * mm);
+  double* S = h->c.arena.alloc((long long)nc * chi);
+  const int corners[4] = {C1, C2, C3, C4};
+  long long i = 0;
+  for (int x = 0; x < h->P.Lx; ++x)
+    for (int y = 0; y < h->P.Ly; ++y)
+      for (int k : corners) {
+        const Tensor t = key_view(h, h->store, x, y, k);
+        SCTM_CUDA(cudaMemcpyAsync(M + i * mm, t.data, mm * sizeof(double), cudaMemcpyDeviceToDevice, h->c.stream));
+        ++i;
+      }
+  for (int b0 = 0; b0 < nc; b0 += 64) {   // at most 64 matrices per SVD launch
+    const int nb = std::min(64, nc - b0);
+    const size_t wn = svd_work_doubles(chi, chi, nb);
+    double* work = wn ? h->c.arena.alloc((long long)wn) : nullptr;
+    launch_svd(chi, chi, nb, M + b0 * mm, U + b0 * mm, S + (long long)b0 * chi, V + b0 * mm, work,
+               h->c.svd_status, h->c.stream);
+  }
+  check_svd(h);
+  SCTM_CUDA(cudaMemcpyAsync(out.data(), S, out.size() * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+  SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+  h->c.arena.release(mk);
+  for (int c = 0; c < nc; ++c) {   // S is descending: s[0] is the largest
+    double* s = out.data() + (size_t)c * chi;
+    const double top = s[0];
+    if (top > 0)
+      for (int j = 0; j < chi; ++j) s[j] /= top;
+  }
+  return out;
+}
+
 void sweep_untaped(sctm_handle h) {
   for (int d = 0; d < 4; ++d) {
     size_t mk = h->c.arena.mark();
@@ -373,6 +416,37 @@ int split_ctmrg_sweeps(sctm_handle h, int n) {
     SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
     for (int i = 0; i < n; ++i) sweep_untaped(h);
     check_svd(h);
+  });
+}
+
+int split_ctmrg_run(sctm_handle h, int max_sweeps, double tol, int* sweeps_done, double* last_delta) {
+  return guard(h, [&]() {
+    SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
+    SCTM_CHECK(max_sweeps >= 0, "max_sweeps must be >= 0");
+    if (!(tol > 0)) tol = h->c.fp32_compute ? 1e-7 : 1e-12;
+    const size_t chi = (size_t)h->P.chi;
+    std::vector<double> prev = corner_spectra(h);
+    double delta = HUGE_VAL;
+    int n = 0;
+    while (n < max_sweeps) {
+      sweep_untaped(h);
+      ++n;
+      std::vector<double> cur = corner_spectra(h);
+      delta = 0.0;
+      for (size_t c = 0; c < cur.size() / chi; ++c) {
+        double ss = 0.0;
+        for (size_t j = 0; j < chi; ++j) {
+          const double d = cur[c * chi + j] - prev[c * chi + j];
+          ss += d * d;
+        }
+        if (!std::isfinite(ss)) throw std::runtime_error("non-finite corner spectrum");
+        delta = std::max(delta, std::sqrt(ss));
+      }
+      prev.swap(cur);
+      if (delta < tol) break;
+    }
+    if (sweeps_done) *sweeps_done = n;
+    if (last_delta) *last_delta = delta;
   });
 }
 

@@ -243,3 +243,30 @@ def test_conventional_ctmrg_gradient_matches_oracle(S):
     assert abs(e - float(eo)) < 1e-10 * abs(float(eo))
     rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
     assert rel < 1e-7, rel
+
+
+@pytest.mark.parametrize("algorithm", [0, 1])
+def test_run_to_tolerance_matches_oracle(S, algorithm):
+    """split_ctmrg_run (full steps until the normalised corner spectra change
+    by less than tol) stops after the same number of steps as the oracle's
+    ctmrg_run, reports the same last change, and leaves the environment whose
+    energy is the oracle's (1e-10 relative).  The tolerance is the geometric
+    mean of two consecutive oracle changes that are at least 3x apart, so
+    rounding cannot move the step at which either side stops."""
+    Lx, Ly, D, chi = 2, 2, 2, 8
+    A = _near(Lx, Ly, D, 0.2, seed=7)
+    Ac = C.as_cell(A)
+    split = algorithm == 0
+    _, _, hist = C.ctmrg_run(Ac, chi, 0.0, 12, split=split)
+    k = next(i for i in range(4, len(hist) - 1) if min(hist[:i + 1]) > 3 * hist[i + 1])
+    tol = (hist[k] * hist[k + 1]) ** 0.5
+    env_o, n_o, d_o = C.ctmrg_run(Ac, chi, tol, 12, split=split)
+    assert n_o == k + 2
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, algorithm=algorithm) as s:
+        s.init(torch.tensor(A, device="cuda"))
+        n, delta = s.run(12, tol)
+        e_gpu = s.energy(H, 0.5 * H)
+    assert n == n_o, (n, n_o, hist)
+    assert abs(delta - d_o[-1]) < 1e-3 * d_o[-1], (delta, d_o[-1])
+    e_or = float(En.energy_per_site(Ac, env_o, H, 0.5 * H, split=split))
+    assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)

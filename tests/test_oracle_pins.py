@@ -188,6 +188,30 @@ def test_ising_peps_matches_onsager(split):
         assert abs(float(bonds[(0, 0)][k]) - ref) < 5e-7, k
 
 
+@pytest.mark.parametrize("split", [True, False])
+def test_run_to_fixed_point_matches_onsager(split):
+    """Iterating full steps until the normalised corner spectra stop changing
+    (ctmrg_run) reaches the true fixed point: for the Ising PEPS off
+    criticality the change per step decays geometrically, the run stops on its
+    own, and the converged correlator is Onsager's exact value."""
+    beta = 0.3
+    A = C.as_cell(I.gauge_transform_cell(_ising_peps(beta), seed=3, scale=0.4))
+    env, n, hist = C.ctmrg_run(A, 12, 1e-9, 60, split=split)
+    assert n < 60 and hist[-1] < 1e-9 and min(hist[:-1]) >= 1e-9
+    assert all(b < a for a, b in zip(hist[2:], hist[3:])), hist
+    ZZ = np.kron(np.diag([1.0, -1.0]), np.diag([1.0, -1.0]))
+    _, bonds = En.energy_per_site(A, env, ZZ, split=split, return_bonds=True)
+    assert abs(float(bonds[(0, 0)]["top"]) - _onsager_nn(beta)) < 5e-7
+
+
+def test_run_stops_at_once_for_a_product_state():
+    """A D=1 product state has rank-one corners: their normalised spectrum is
+    (1, 0, ...) from the start, so the first step already changes nothing."""
+    A = C.as_cell(np.array([0.8, 0.6]).reshape(1, 1, 2, 1, 1, 1, 1))
+    _, n, hist = C.ctmrg_run(A, 4, 1e-12, 10)
+    assert n == 1 and hist[0] < 1e-15
+
+
 def _near_product(Lx, Ly, D, eps, seed):
     rng = np.random.default_rng(seed)
     A0 = np.zeros((Lx, Ly, 2, D, D, D, D))
