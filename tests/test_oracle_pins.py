@@ -249,6 +249,21 @@ def test_energy_converges_monotonically_in_chi(split):
     assert abs(E[16] - E[20]) < 1e-10
 
 
+def test_split_conventional_gap_closes_with_chi():
+    """The split and the conventional CTMRG approximate the same contraction
+    with different truncations, so their energies approach each other as chi
+    grows (Sec. III, Fig. 4a): on a random D=2 state the gap falls at every step
+    chi = 2, 4, 8, 12, 16, 20, by five orders of magnitude in all."""
+    A = C.as_cell(I.random_cell(1, 1, 2, 2, seed=0))
+    gap = []
+    for chi in (2, 4, 8, 12, 16, 20):
+        e_s = float(En.energy_per_site(A, C.split_ctmrg(A, chi, 30), HR))
+        e_c = float(En.energy_per_site(A, C.conv_ctmrg(A, chi, 30), HR, split=False))
+        gap.append(abs(e_s - e_c))
+    assert all(b < a for a, b in zip(gap, gap[1:])), gap
+    assert gap[0] > 1e-2 and gap[-1] < 1e-6, gap
+
+
 def test_rotation_and_gauge_invariance():
     """The energy of an isotropic Hamiltonian does not change when the lattice
     is rotated by 90 degrees or when gauge matrices are put on every bond
