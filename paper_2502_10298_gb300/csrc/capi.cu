@@ -42,18 +42,24 @@ int fail(sctm_handle h, int code, const std::string& msg) {
   return code;
 }
 
+void rollback(sctm_handle h, size_t arena_mark);
+
 template <typename F>
 int guard(sctm_handle h, F&& f) {
   if (!h) return SCTM_ERR_ARG;
+  const size_t mk = h->c.arena.mark();
   try {
     f();
     return SCTM_OK;
   } catch (const ArgError& e) {
+    rollback(h, mk);
     std::string m = e.what();
     return fail(h, m.find("workspace exhausted") != std::string::npos ? SCTM_ERR_OOM : SCTM_ERR_ARG, m);
   } catch (const CudaError& e) {
+    rollback(h, mk);
     return fail(h, SCTM_ERR_CUDA, e.what());
   } catch (const std::exception& e) {
+    rollback(h, mk);
     std::string m = e.what();
     if (m.find("no convergence") != std::string::npos) return fail(h, SCTM_ERR_SVD_NOCONV, m);
     if (m.find("non-finite") != std::string::npos) return fail(h, SCTM_ERR_NONFINITE, m);
@@ -117,6 +123,19 @@ void bind_store(sctm_handle h, double* base) {
   for (int x = 0; x < h->P.Lx; ++x)
     for (int y = 0; y < h->P.Ly; ++y)
       for (int k = 0; k < NKEY; ++k) h->cell.e(x, y)[k] = key_view(h, base, x, y, k);
+}
+
+// A call that failed part-way leaves nothing behind: its workspace is released,
+// its tape dropped, and the handles point at the persistent store again (which
+// holds the environment of the last call that completed).
+void rollback(sctm_handle h, size_t arena_mark) {
+  h->c.arena.release(arena_mark);
+  h->c.tape.active = false;
+  h->c.tape.ops.clear();
+  if (h->store && h->A) {
+    bind_A(h, false);
+    bind_store(h, h->store);
+  }
 }
 
 // leaves for a taped region: arena copies of `base` with zeroed gradients
@@ -567,22 +586,27 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
 
 int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const double* h_nn_host,
                      const double* h_diag_host, double* e_per_site, double* grad_host) {
-  return guard(h, [&]() {
-    SCTM_CHECK(A_cell_host && grad_host, "null argument");
-    const Params& P = h->P;
-    const long long nA = (long long)P.Lx * P.Ly * P.p * (long long)P.D * P.D * P.D * P.D;
-    size_t mk = h->c.arena.mark();
-    double* a = h->c.arena.alloc(nA);
-    double* g = h->c.arena.alloc(nA);
-    size_t inner = h->c.arena.mark();
+  if (!h) return SCTM_ERR_ARG;
+  if (!A_cell_host || !grad_host) return fail(h, SCTM_ERR_ARG, "null argument");
+  const Params& P = h->P;
+  const long long nA = (long long)P.Lx * P.Ly * P.p * (long long)P.D * P.D * P.D * P.D;
+  const size_t mk = h->c.arena.mark();
+  double* a = nullptr;
+  double* g = nullptr;
+  int rc = guard(h, [&]() {
+    a = h->c.arena.alloc(nA);
+    g = h->c.arena.alloc(nA);
     SCTM_CUDA(cudaMemcpyAsync(a, A_cell_host, nA * sizeof(double), cudaMemcpyHostToDevice, h->c.stream));
-    int rc = energy_grad(h, a, sweeps, h_nn_host, h_diag_host, e_per_site, g);
-    if (rc != SCTM_OK) throw std::runtime_error(h->err);
-    (void)inner;
-    SCTM_CUDA(cudaMemcpyAsync(grad_host, g, nA * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
-    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
-    h->c.arena.release(mk);
   });
+  // energy_grad's own error code (e.g. SCTM_ERR_OOM) is passed through unchanged
+  if (rc == SCTM_OK) rc = energy_grad(h, a, sweeps, h_nn_host, h_diag_host, e_per_site, g);
+  if (rc == SCTM_OK)
+    rc = guard(h, [&]() {
+      SCTM_CUDA(cudaMemcpyAsync(grad_host, g, nA * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+      SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+    });
+  h->c.arena.release(mk);
+  return rc;
 }
 
 int sctm_get_env(sctm_handle h, int x, int y, double* out_dev) {

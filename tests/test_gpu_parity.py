@@ -270,3 +270,27 @@ def test_run_to_tolerance_matches_oracle(S, algorithm):
     assert abs(delta - d_o[-1]) < 1e-3 * d_o[-1], (delta, d_o[-1])
     e_or = float(En.energy_per_site(Ac, env_o, H, 0.5 * H, split=split))
     assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
+
+
+def test_failed_call_leaves_handle_usable(S):
+    """A call that runs out of device workspace returns SCTM_ERR_OOM, through the
+    device and the host-buffer entry points alike, and the handle then goes on to
+    give the oracle's results: a failed call leaves no workspace, tape or
+    half-updated environment behind."""
+    Lx, Ly, D, chi = 1, 1, 2, 8
+    A = _near(Lx, Ly, D, 0.3, seed=13)
+    At = torch.tensor(A, device="cuda")
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, workspace_bytes=64 << 20) as s:
+        # 4 x 5000 environment checkpoints (about 200 MB) do not fit in 64 MiB
+        with pytest.raises(S.SctmError) as ei:
+            s.energy_grad(At, 5000, HR, None)
+        assert ei.value.code == -5
+        with pytest.raises(S.SctmError) as ei:
+            S.energy_grad_host(s.h, A, 5000, HR, None)
+        assert ei.value.code == -5
+        s.init(At)
+        s.sweeps(3)
+        e_gpu = s.energy(HR, None)
+    Ac = C.as_cell(A)
+    e_or = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, 3), HR, None))
+    assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
