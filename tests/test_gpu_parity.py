@@ -294,3 +294,16 @@ def test_failed_call_leaves_handle_usable(S):
     Ac = C.as_cell(A)
     e_or = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, 3), HR, None))
     assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
+
+
+def test_energy_grad_host_matches_device_call(S):
+    """The host-buffer entry point (the end-to-end call of the benchmark) gives
+    the energy and gradient of the device-buffer call on the same input."""
+    Lx, Ly, D, chi = 2, 2, 2, 8
+    A = _near(Lx, Ly, D, 0.3, seed=21)
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi) as s:
+        e_d, g_d = s.energy_grad(torch.tensor(A, device="cuda"), 2, H, 0.5 * H)
+        e_h, g_h = S.energy_grad_host(s.h, A, 2, H, 0.5 * H)
+    assert abs(e_h - e_d) < 1e-12 * abs(e_d)
+    g_d = g_d.cpu().numpy()
+    assert np.linalg.norm(g_h - g_d) < 1e-10 * np.linalg.norm(g_d)
