@@ -306,4 +306,5 @@ def test_energy_grad_host_matches_device_call(S):
         e_h, g_h = S.energy_grad_host(s.h, A, 2, H, 0.5 * H)
     assert abs(e_h - e_d) < 1e-12 * abs(e_d)
     g_d = g_d.cpu().numpy()
-    assert np.linalg.norm(g_h - g_d) < 1e-10 * np.linalg.norm(g_d)
+    # split-K partial sums are added with atomics: rounding order may differ between calls
+    assert np.linalg.norm(g_h - g_d) < 1e-9 * np.linalg.norm(g_d)
