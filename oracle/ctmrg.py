@@ -28,7 +28,9 @@ site ``env[x][y]`` (x row, y column); the left move writes column y+1 from colum
 Readings where the paper is silent (each also listed in the design doc):
 
 * initial environment: double-layer corners/edges of the neighbouring A, edges
-  split into ket/bra halves by an SVD truncated to chi;
+  split into ket/bra halves by an SVD truncated to chi_I;
+* bond dimensions: ``chi`` is chi_E = chi_I or a pair (chi_E, chi_I); green and
+  teal truncate to chi_E, yellow and red to chi_I (``chi_pair``);
 * projector: keep min(chi, n) singular values, s^{-1/2} -> 0 for s < 1e-8 s_max
   (a smaller cutoff keeps directions amplified by s^{-1/2} > 1e4 and makes the
   map numerically non-differentiable);
@@ -55,6 +57,16 @@ CONV_KEYS = ("C1", "T1", "C2", "T2", "C3", "T3", "C4", "T4")
 CUTOFF = 1e-8
 EPS_L = 1e-36
 es = torch.einsum
+
+
+def chi_pair(chi):
+    """(chi_E, chi_I): environment and interlayer bond dimensions.  An int sets
+    both (chi_E = chi_I, the paper's default); a pair sets them separately
+    (Sec. II.B: the split edges carry chi_E on their environment legs and chi_I
+    on the bond between the ket and the bra edge)."""
+    if isinstance(chi, (tuple, list)):
+        return int(chi[0]), int(chi[1])
+    return int(chi), int(chi)
 
 
 # ----------------------------------------------------------------------- utils
@@ -189,10 +201,11 @@ def initial_env(A, chi: int, split: bool = True):
             if not split:
                 env[x][y] = dict(C1=C1, T1=T1, C2=C2, T2=T2, C3=C3, T3=T3, C4=C4, T4=T4)
                 continue
-            T1k, T1b = _split_edge(T1, chi)
-            T2k, T2b = _split_edge(T2, chi)
-            T3b, T3k = _split_edge(T3, chi)
-            T4b, T4k = _split_edge(T4, chi)
+            chi_i = chi_pair(chi)[1]   # the split cuts the interlayer bond
+            T1k, T1b = _split_edge(T1, chi_i)
+            T2k, T2b = _split_edge(T2, chi_i)
+            T3b, T3k = _split_edge(T3, chi_i)
+            T4b, T4k = _split_edge(T4, chi_i)
             env[x][y] = dict(C1=C1, T1k=T1k, T1b=T1b, C2=C2, T2k=T2k, T2b=T2b,
                              C3=C3, T3b=T3b, T3k=T3k, C4=C4, T4b=T4b, T4k=T4k)
     return env
@@ -497,15 +510,16 @@ def split_column_projectors(A, env, y, chi, record=None):
     a2 = [A[x][yp] for x in range(Lx)]
     D = a[0].shape[1]
     p = a[0].shape[0]
+    chi_e, chi_i = chi_pair(chi)   # green, teal cut E-bands; yellow, red cut I-bands
     Pg, Py = [], []
     for x in range(Lx):
         xp = (x + 1) % Lx
-        up, dn, s = projector_pair(green_rhoT(E[x], a[x]), green_rhoB(E[xp], a[xp]), chi)
+        up, dn, s = projector_pair(green_rhoT(E[x], a[x]), green_rhoB(E[xp], a[xp]), chi_e)
         Pg.append(_pair_tensors(up, dn, (E[x]["T4b"].shape[0], D)))
         if record is not None:
             record.setdefault("green", []).append((up, dn, s))
     for x in range(Lx):
-        up, dn, s = projector_pair(yellow_rhoT(E[x], a[x]), yellow_rhoB(E[x], a[x]), chi)
+        up, dn, s = projector_pair(yellow_rhoT(E[x], a[x]), yellow_rhoB(E[x], a[x]), chi_i)
         Py.append(_pair_tensors(up, dn, (E[x]["T4k"].shape[0], D)))
         if record is not None:
             record.setdefault("yellow", []).append((up, dn, s))
@@ -514,13 +528,13 @@ def split_column_projectors(A, env, y, chi, record=None):
     for x in range(Lx):
         xp = (x + 1) % Lx
         up, dn, s = projector_pair(teal_rhoT(E[x], a[x], K[x], E2[x], a2[x]),
-                                   teal_rhoB(E[xp], a[xp], K[xp], E2[xp], a2[xp]), chi)
+                                   teal_rhoB(E[xp], a[xp], K[xp], E2[xp], a2[xp]), chi_e)
         Pt.append(_pair_tensors(up, dn, (K[x]["T4bk"].shape[2], D)))
         if record is not None:
             record.setdefault("teal", []).append((up, dn, s))
     for x in range(Lx):
         up, dn, s = projector_pair(red_rhoT(E[x], K[x], E2[x], a2[x]),
-                                   red_rhoB(E[x], a[x], K[x], E2[x], a2[x]), chi)
+                                   red_rhoB(E[x], a[x], K[x], E2[x], a2[x]), chi_i)
         Pr.append(_pair_tensors(up, dn, (K[x]["T4kk"].shape[2], p, D)))
         if record is not None:
             record.setdefault("red", []).append((up, dn, s))
@@ -641,7 +655,7 @@ def conv_left_move(A, env, chi, record=None):
             TR = corner_TR(env[x][yp], A[x][yp])
             BL = corner_BL(env[xp][y], A[xp][y])
             BR = corner_BR(env[xp][yp], A[xp][yp])
-            up, dn, s = projector_pair(TL.T @ TR, BR @ BL.T, chi)
+            up, dn, s = projector_pair(TL.T @ TR, BR @ BL.T, chi_pair(chi)[0])
             n = env[x][y]["T4"].shape[0]
             D = A[x][y].shape[1]
             k = up.shape[0]
@@ -695,6 +709,7 @@ def conv_ctmrg(A, chi: int, sweeps: int, env=None):
 def corner_spectra(env, chi: int):
     """Singular values of the four corners of every site, each divided by its
     largest and padded with zeros to chi (the oracle's corners grow to chi)."""
+    chi = chi_pair(chi)[0]   # corners carry environment bonds only
     out = []
     for row in env:
         for e in row:

@@ -264,6 +264,29 @@ def test_split_conventional_gap_closes_with_chi():
     assert gap[0] > 1e-2 and gap[-1] < 1e-6, gap
 
 
+def test_interlayer_bond_dimension():
+    """chi_I (the bond between a ket and a bra edge) is truncated separately
+    from chi_E (Sec. II.B): the split edges are [chi_E, D, chi_I] and
+    [chi_I, D, chi_E]; at fixed chi_E the energy approaches its chi_I = chi_E
+    value as chi_I grows (Sec. III, Fig. 4b), and a pair (chi, chi) is the
+    same computation as chi."""
+    A = C.as_cell(_near_product(1, 1, 2, 0.25, seed=5))
+    chi_e = 12
+    E = {}
+    for chi_i in (2, 4, 6, 8, 12):
+        env = C.split_ctmrg(A, (chi_e, chi_i), 30)
+        e = env[0][0]
+        assert e["T1k"].shape[0] == e["T1b"].shape[2] == chi_e
+        assert e["T1k"].shape[2] == e["T1b"].shape[0] <= chi_i
+        assert e["T4b"].shape[0] == e["T4k"].shape[2] == chi_e
+        assert e["T4b"].shape[2] == e["T4k"].shape[0] <= chi_i
+        E[chi_i] = float(En.energy_per_site(A, env, HR))
+    err = [abs(E[c] - E[chi_e]) for c in (2, 4, 6, 8)]
+    assert all(b < a for a, b in zip(err, err[1:])) and err[-1] < 1e-5, err
+    assert float(En.energy_per_site(A, C.split_ctmrg(A, (8, 8), 5), HR)) == \
+        float(En.energy_per_site(A, C.split_ctmrg(A, 8, 5), HR))
+
+
 def test_rotation_and_gauge_invariance():
     """The energy of an isotropic Hamiltonian does not change when the lattice
     is rotated by 90 degrees or when gauge matrices are put on every bond
