@@ -9,6 +9,7 @@
 namespace sctm {
 
 constexpr int kMaxDims = 8;    // dims of one index group (batch / m / n / k)
+constexpr int kNumSMs = 152;   // GB300: two dies of 76 SMs; grid-size heuristics count in these
 
 // Error carried from a CUDA call into the C-ABI status code.
 struct CudaError : std::runtime_error {

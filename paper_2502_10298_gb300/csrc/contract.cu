@@ -143,7 +143,7 @@ void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, con
   const long long total = d.B * d.M * d.N;
   if (total == 0) return;
   ProfScope pf(PF_MISC, s, 0.0, 8.0 * total * (d.beta != 0 ? 3 : 2));
-  const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 148 * 16);
+  const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, kNumSMs * 16);
   splitk_finish_kernel<<<blocks, 256, 0, s>>>(d, Wm, Wn, W, C);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -155,7 +155,7 @@ constexpr int kCBM = 64, kCBN = 64, kCBK = 16;
 // multiply-adds per clock and a small output must still occupy every SM
 long long contract_splits(const ContractDesc& d) {
   const long long tiles = ((d.M + kCBM - 1) / kCBM) * ((d.N + kCBN - 1) / kCBN) * d.B;
-  const long long want = (2 * 148 + tiles - 1) / tiles;
+  const long long want = (2 * kNumSMs + tiles - 1) / tiles;
   long long sp = std::min<long long>(want, d.K / kCBK);
   if (sp < 2 || d.B > 65535) return 1;
   return std::min<long long>(sp, 65535);

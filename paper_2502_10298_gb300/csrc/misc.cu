@@ -25,7 +25,7 @@ __global__ void copy_kernel(Group g, long long total, T alpha, const T* __restri
 
 static unsigned grid_for(long long total) {
   long long g = (total + kThreads - 1) / kThreads;
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > kNumSMs * 32) g = kNumSMs * 32;
   if (g < 1) g = 1;
   return (unsigned)g;
 }
@@ -397,7 +397,7 @@ void launch_scale_dim_reduce(const Group& g, int dim, const double* a, const dou
   const long long sz = g.size[dim];
   const long long per_j = total / sz;
   const unsigned ys = (unsigned)std::max<long long>(1, std::min<long long>((per_j + kThreads - 1) / kThreads,
-                                                                           (152 * 8 + sz - 1) / sz));
+                                                                           (kNumSMs * 8 + sz - 1) / sz));
   scale_dim_reduce_kernel<<<dim3((unsigned)sz, ys), kThreads, 0, s>>>(g, dim, a, b, vbar);
   SCTM_CUDA(cudaGetLastError());
 }

@@ -432,7 +432,7 @@ bool tc_eligible(const ContractDesc& d) {
 static int tc_splits(const ContractDesc& d) {
   const long long tiles = (round_up(d.M, TC_BM) / TC_BM) * (round_up(d.N, TC_BN) / TC_BN) * d.B;
   const long long nk = round_up(d.K, TC_BK) / TC_BK;
-  const long long want = (2 * 148 + tiles - 1) / tiles;
+  const long long want = (2 * kNumSMs + tiles - 1) / tiles;
   long long sp = std::min<long long>(want, nk / 4);
   if (sp < 2) return 1;
   const long long per = (nk + sp - 1) / sp;
