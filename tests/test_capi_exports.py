@@ -29,3 +29,38 @@ def test_library_builds_and_exports_declared_symbols():
 def test_binding_signatures_load():
     import paper_2502_10298_gb300 as S
     S.load_library()
+
+
+def _header_source():
+    src = "\n".join(open(h).read() for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    return re.sub(r"/\*.*?\*/", "", src, flags=re.S)   # drop comments
+
+
+def test_binding_argument_counts_match_header():
+    """Every declared entry point has a ctypes signature with as many arguments
+    as its prototype, so the binding cannot drift from the header."""
+    import paper_2502_10298_gb300 as S
+    lib = S.load_library()
+    protos = {}
+    for m in re.finditer(r"^SCTM_API\s+[\w\s\*]*?\b(\w+)\s*\(([^)]*)\)\s*;", _header_source(), flags=re.M):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        protos[m.group(1)] = len(params)
+    assert protos.keys() == declared_symbols()
+    for name, n in protos.items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+
+
+def test_config_struct_matches_header():
+    """The ctypes Config lists the fields of sctm_config in the header's order."""
+    import paper_2502_10298_gb300 as S
+    body = re.search(r"typedef\s+struct\s*\{(.*?)\}\s*sctm_config\s*;", _header_source(), flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1]   # drop the type
+        fields += [n.strip().lstrip("*") for n in names.split(",")]
+    assert [f for f, _ in S.Config._fields_] == fields
