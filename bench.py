@@ -4,7 +4,7 @@ One step = one call of the engine's ``energy_grad``: initial environment,
 `sweeps` full directional steps (left, top, right, bottom), 2x2-patch energy,
 and the reverse pass through all of it.  Workload (default): 2x2 cell, d=2,
 D=8, chi=128, J1-J2 Heisenberg with J2/J1=0.5, seeded N(0,1) tensors with a
-Neel-biased component (synthetic; ipeps_inputs.config("cfg4")).
+Neel-biased component (synthetic; ipeps_inputs.config("d8_chi128_2x2_j1j2")).
 
 Prints one JSON line (rank 0).  Run ``--impl reference`` to time the FP64 CPU
 oracle on the same workload (bounded sample, host cores).
@@ -212,7 +212,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg4")
+    ap.add_argument("--config", default="d8_chi128_2x2_j1j2", choices=sorted(I.WORKLOADS))
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP64, 1 mixed (3xTF32 tensor cores), 2 mixed on CUDA cores; default per workload")

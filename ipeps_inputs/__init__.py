@@ -15,7 +15,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "random_cell", "neel_biased_cell", "config", "CONFIGS",
+    "random_cell", "neel_biased_cell", "config", "WORKLOADS",
     "pauli", "heisenberg_bond", "heisenberg_bond_rotated",
     "product_state_cell", "plaquette_cell", "dimer_cell", "dimer_pairs_cell",
     "gauge_transform_cell", "rotate_cell_90",
@@ -53,20 +53,25 @@ def neel_biased_cell(p: int, D: int, seed: int = 0, bias: float = 0.5) -> np.nda
     return A
 
 
-# Workloads: (name, Lx, Ly, p, D, chi, model, J2, rotated)
-CONFIGS = {
-    "cfg1": dict(Lx=1, Ly=1, p=2, D=2, chi=16, J2=0.0, rotated=True, sweeps=30, bench_sweeps=30),
-    "cfg2": dict(Lx=2, Ly=2, p=2, D=4, chi=32, J2=0.0, rotated=False, sweeps=30, bench_sweeps=4),
-    "cfg3": dict(Lx=2, Ly=2, p=2, D=6, chi=72, J2=0.0, rotated=False, sweeps=20, bench_sweeps=2, bench_precision=1),
-    "cfg4": dict(Lx=2, Ly=2, p=2, D=8, chi=128, J2=0.5, rotated=False, sweeps=10, bench_sweeps=1, bench_precision=1),
-    "cfg5": dict(Lx=1, Ly=1, p=2, D=10, chi=200, J2=0.0, rotated=True, sweeps=10, bench_sweeps=1, bench_precision=1),
+# Workloads, named by bond dimension, environment dimension, unit cell and model:
+# cell Lx x Ly, physical dimension p, D, chi, J2 / J1 of the diagonal bonds,
+# rotated (sublattice-rotated bond operator of 1-site cells), neel (Neel bias)
+WORKLOADS = {
+    "d2_chi16_1x1": dict(Lx=1, Ly=1, p=2, D=2, chi=16, J2=0.0, rotated=True, sweeps=30, bench_sweeps=30),
+    "d4_chi32_2x2": dict(Lx=2, Ly=2, p=2, D=4, chi=32, J2=0.0, rotated=False, sweeps=30, bench_sweeps=4),
+    "d6_chi72_2x2": dict(Lx=2, Ly=2, p=2, D=6, chi=72, J2=0.0, rotated=False, sweeps=20, bench_sweeps=2,
+                         bench_precision=1),
+    "d8_chi128_2x2_j1j2": dict(Lx=2, Ly=2, p=2, D=8, chi=128, J2=0.5, rotated=False, sweeps=10, bench_sweeps=1,
+                               bench_precision=1, neel=True),
+    "d10_chi200_1x1": dict(Lx=1, Ly=1, p=2, D=10, chi=200, J2=0.0, rotated=True, sweeps=10, bench_sweeps=1,
+                           bench_precision=1),
 }
 
 
 def config(name: str):
     """Return (A_cell, params) for a named workload; inputs are seeded (seed 0)."""
-    c = dict(CONFIGS[name])
-    if name == "cfg4":
+    c = dict(WORKLOADS[name])
+    if c.get("neel"):
         A = neel_biased_cell(c["p"], c["D"], seed=0)
     else:
         A = random_cell(c["Lx"], c["Ly"], c["p"], c["D"], seed=0)

@@ -71,9 +71,9 @@ def test_sweeps_environment_and_energy(S, Lx, Ly, D, chi):
         assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
 
 
-def test_config1_energy(S):
+def test_d2_chi16_thirty_sweeps_energy(S):
     """1x1, d=2, D=2, chi=16, 30 sweeps (rotated Heisenberg): energy vs oracle."""
-    A, c = I.config("cfg1")
+    A, c = I.config("d2_chi16_1x1")
     with S.SplitCTMRG(1, 1, 2, 2, 16) as s:
         s.init(torch.tensor(A, device="cuda"))
         s.sweeps(30)
