@@ -308,3 +308,32 @@ def test_energy_grad_host_matches_device_call(S):
     g_d = g_d.cpu().numpy()
     # split-K partial sums are added with atomics: rounding order may differ between calls
     assert np.linalg.norm(g_h - g_d) < 1e-9 * np.linalg.norm(g_d)
+
+
+def test_full_size_gradient_is_the_derivative_of_the_energy(S):
+    """At the benchmark's size and settings (D=8, chi=128, 2x2 J1-J2 with
+    J2/J1 = 0.5, one sweep, mixed precision) the oracle cannot run, so a
+    property that holds at any size stands in: the gradient is the derivative of
+    the energy the engine computes.  A central difference along the unit vector
+    g/|g| (step 1e-3 on a cell with max |A| = 1) must give |g|; the forward-only
+    calls must reproduce the energy of the gradient call."""
+    A, c = I.config("d8_chi128_2x2_j1j2")
+    h, hd = H, c["J2"] * H
+    At = torch.tensor(A, device="cuda")
+    step = 1e-3
+    with S.SplitCTMRG(2, 2, 2, 8, 128, precision=1, workspace_bytes=100 << 30) as s:
+        e0, g = s.energy_grad(At, 1, h, hd)
+        gn = float(g.norm())
+        v = g / gn
+
+        def energy(X):
+            s.init(X)
+            s.sweeps(1)
+            return s.energy(h, hd)
+
+        e_fwd = energy(At)
+        ep, em = energy(At + step * v), energy(At - step * v)
+    assert np.isfinite(e0) and np.isfinite(gn) and gn > 0
+    assert abs(e_fwd - e0) < 1e-6, (e_fwd, e0)
+    fd = (ep - em) / (2 * step)
+    assert abs(fd - gn) < 0.1 * gn, (fd, gn)
