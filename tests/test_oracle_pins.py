@@ -12,6 +12,7 @@ import ipeps_inputs as I
 from oracle import ctmrg as C
 from oracle import energy as En
 from oracle import statevector as SV
+from oracle.fixed_point import implicit_energy_grad
 from oracle.svd import svd as osvd
 
 H = I.heisenberg_bond()
@@ -285,6 +286,39 @@ def test_interlayer_bond_dimension():
     assert all(b < a for a, b in zip(err, err[1:])) and err[-1] < 1e-5, err
     assert float(En.energy_per_site(A, C.split_ctmrg(A, (8, 8), 5), HR)) == \
         float(En.energy_per_site(A, C.split_ctmrg(A, 8, 5), HR))
+
+
+def test_implicit_gradient_matches_unrolled_and_finite_differences():
+    """The implicit (fixed-point) gradient of the converged energy equals the
+    gradient taken through 30 unrolled steps, whose transient has died out, and
+    a central difference of the converged energy along a random direction."""
+    A = _near_product(1, 1, 2, 0.25, seed=5)
+    chi = 8
+    E, g, info = implicit_energy_grad(A, chi, HR)
+    assert info["solver_iterations"] < 100
+    At = torch.tensor(A).requires_grad_(True)
+    Ac = [[At[0, 0]]]
+    e = En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, 30), HR)
+    e.backward()
+    assert abs(float(e.detach()) - E) < 1e-12
+    assert float((At.grad - g).norm() / g.norm()) < 1e-10
+    v = np.random.default_rng(1).standard_normal(A.shape)
+    v /= np.linalg.norm(v)
+    eps = 1e-5
+
+    def converged(X):
+        env, _, _ = C.ctmrg_run(X, chi, 1e-14, 300)
+        return float(En.energy_per_site(C.as_cell(X), env, HR))
+    fd = (converged(A + eps * v) - converged(A - eps * v)) / (2 * eps)
+    assert abs(fd - float((g.numpy() * v).sum())) < 1e-7 * abs(fd)
+
+
+def test_implicit_gradient_refuses_a_gauge_that_is_not_fixed():
+    """The conventional scheme's tensors flip signs between steps even when its
+    corner spectra have converged; the fixed-point rule does not apply there."""
+    A = _near_product(1, 1, 2, 0.25, seed=5)
+    with pytest.raises(ValueError):
+        implicit_energy_grad(A, 8, HR, split=False, max_sweeps=40)
 
 
 def test_rotation_and_gauge_invariance():
