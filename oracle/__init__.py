@@ -16,12 +16,17 @@ provides an independent reference gradient.  Modules:
                      the conventional double-layer CTMRG with 2x2-patch projectors,
                      the frame maps that turn a left move into the other three
                      directions, and the directional sweep.
+                     Also the run to a fixed point (``ctmrg_run``, corner spectra)
+                     and separate environment / interlayer dimensions (``chi_pair``).
 * ``energy``      -- 2x2-patch energy from the (fused) environment.
 * ``statevector`` -- brute-force expectation values of small cluster states.
+* ``fixed_point`` -- the energy gradient by implicit differentiation of the
+                     converged environment.
 
-Parity status: every function is pinned by ``tests/test_oracle_pins.py`` except
-the teal/red rho networks, whose figures are missing from the paper; those follow
-a documented reading and their exact form is "parity unpinned" against the paper
-(their correctness as projectors is pinned by the projector identities and by
-the exactly solvable cluster states).
+Parity status: every function is pinned by ``tests/test_oracle_pins.py``.  The
+teal/red rho networks follow a documented reading (their figures are missing
+from the paper); they are pinned as parts of the method -- by the projector
+identities, Onsager's exact correlator, the exactly solvable cluster states and
+the split/conventional agreement -- while their literal match to the missing
+figures cannot be checked.
 """
