@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 import ipeps_inputs as I  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe's nominal figure)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal (about 152 SMs x 2.07 GHz x 4 flop/clk/SM)
 TC_CORNER_DRAM_BYTES = 6.576915e9 + 0.52181376e9   # ncu, tc_gemm_kernel on one 8192^3 product
 
 
@@ -153,6 +153,48 @@ def cpu_baseline(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
                       f"({t_prod:.2f} s) at {name} on the host; scaled to one energy+gradient evaluation "
                       f"as 3x the forward ({moves} moves x {cols_per_move} columns + {50 * n_patch} corner "
                       f"products of the 2x2 energy)"}
+
+
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+
+
+def roofline_of(fam, p, peaks, src, prec):
+    """Roofline of the dominant kernel family `fam` of a step, from the engine's
+    profiler record p = {ms, launches, flops, bytes} over the timed steps.
+
+    tensor: the 3xTF32 tcgen05 contraction against the TF32 peak (the measured
+    bf16 figure, sustained, times the nominal TF32/BF16 ratio 1.1/2.25); achieved
+    counts the algorithmic 2MNK only, while the pipe executes three TF32 products
+    per multiply-add.  svd, and contract at precisions 0 and 3: FP64 ALU.
+    contract at precisions 1 and 2: FP32 ALU (its FP64 Gram products are the
+    smaller part).  other (packing, copies, scaling): HBM bytes against the
+    measured copy bandwidth."""
+    ms = p["ms"]
+    if fam == "other":
+        achieved = p["bytes"] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        peak = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "other (packing, copies, scaling)",
+                "peak_source": f"{src} copy bandwidth"}
+    achieved = p["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    if fam == "tensor":
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        peak = bf16 * 1.1 / 2.25
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                # DRAM bytes (read + write) of one 8192^3 enlarged-corner product, the kernel's
+                # dominant launch shape, from one ncu capture of the current kernel
+                "traffic": TC_CORNER_DRAM_BYTES,
+                "traffic_launch": "8192^3 corner product (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "kernel": "tc_gemm_kernel (3xTF32 tcgen05 contraction)",
+                "peak_source": f"TF32 = {src} bf16 sustained x 1.1/2.25 (nominal ratio)",
+                "tensor_pipe_frac": 3.0 * achieved / peak}
+    if fam == "contract" and prec in (1, 2):
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_NOMINAL_TFLOPS, "traffic": None, "kernel": "contract_kernel (FP32 ALU)",
+                "peak_source": "FP32 nominal (152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz); none measured"}
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": fam + " (FP64 ALU)",
+            "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM); no FP64 figure measured"}
 
 
 def arm_config(desc, prec, world):
@@ -309,25 +351,7 @@ def main():
             for k, v in prof.items()}
     fam = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[fam]
-    achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else 0.0
-    if fam == "tensor":
-        # TF32 tensor peak: the measured bf16 figure (sustained: the kernel runs inside a long step)
-        # times the nominal TF32/BF16 ratio 1.1/2.25; achieved counts the algorithmic 2MNK only,
-        # while the 3xTF32 split executes three tensor products per multiply-add
-        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        peak = bf16 * 1.1 / 2.25
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                # DRAM bytes (read + write) of one 8192^3 enlarged-corner product, the kernel's
-                # dominant launch shape, from one ncu capture of the current kernel
-                "traffic": TC_CORNER_DRAM_BYTES,
-                "traffic_launch": "8192^3 corner product (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "kernel": "tc_gemm_kernel (3xTF32 tcgen05 contraction)",
-                "peak_source": f"TF32 = {src} bf16 sustained x 1.1/2.25 (nominal ratio)",
-                "tensor_pipe_frac": 3.0 * achieved / peak}
-    else:
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": fam,
-                "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM); no FP64 figure measured"}
+    roof = roofline_of(fam, p, peaks, src, prec)
     roof["share_of_device_time"] = p["ms"] / tot_ms if tot_ms else None
     roof["families"] = fams
     cpu = None
