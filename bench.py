@@ -266,6 +266,8 @@ def main():
     ap.add_argument("--move-scaling", action="store_true",
                     help="time one directional move of the split and the conventional CTMRG against D at "
                          "fixed chi (the paper's Fig. 5a comparison) instead of the evaluation")
+    ap.add_argument("--chi", type=int, default=128, help="environment dimension of --move-scaling")
+    ap.add_argument("--Ds", default="4,5,6,7,8", help="comma-separated bulk dimensions of --move-scaling")
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
                     help="time one kernel alone instead of the evaluation (profiling aid)")
     ap.add_argument("--workspace-gb", type=float, default=None)
@@ -275,7 +277,7 @@ def main():
     if args.kernel:
         return run_kernel(args)
     if args.move_scaling:
-        return run_move_scaling(args)
+        return run_move_scaling(args, chi=args.chi, Ds=tuple(int(d) for d in args.Ds.split(",")))
 
     import torch
     import paper_2502_10298_gb300 as S
