@@ -266,6 +266,9 @@ def main():
     ap.add_argument("--move-scaling", action="store_true",
                     help="time one directional move of the split and the conventional CTMRG against D at "
                          "fixed chi (the paper's Fig. 5a comparison) instead of the evaluation")
+    ap.add_argument("--forward", action="store_true",
+                    help="time the forward pieces of the workload (initial environment, one move, 2x2 energy) "
+                         "and report the peak device workspace, for workloads whose gradient does not fit")
     ap.add_argument("--chi", type=int, default=128, help="environment dimension of --move-scaling")
     ap.add_argument("--Ds", default="4,5,6,7,8", help="comma-separated bulk dimensions of --move-scaling")
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
@@ -276,6 +279,8 @@ def main():
         return run_reference(args)
     if args.kernel:
         return run_kernel(args)
+    if args.forward:
+        return run_forward(args)
     if args.move_scaling:
         return run_move_scaling(args, chi=args.chi, Ds=tuple(int(d) for d in args.Ds.split(",")))
 
@@ -406,6 +411,39 @@ def run_kernel(args):
                       "peak_tf32_tflops": peak, "frac": ach / peak, "tensor_pipe_frac": 3 * ach / peak,
                       "pack_ms_per_step": prof["other"]["ms"] / max(1, args.steps),
                       "peak_source": f"{src} bf16 burst x 1.1/2.25"}))
+    return 0
+
+
+def run_forward(args):
+    """Device time (CUDA events) of the initial environment, of one directional
+    move (mean over the second of two sweeps) and of the 2x2 energy for the
+    workload, in the handle's precision, and the peak device workspace."""
+    import torch
+    import paper_2502_10298_gb300 as S
+    A, c, h_nn, h_diag, _, desc = workload(args.config, args.sweeps)
+    prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
+    algo = 1 if args.algorithm == "conventional" else 0
+    At = torch.tensor(A, device="cuda")
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        out = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return out, ev0.elapsed_time(ev1)
+
+    ws = int(args.workspace_gb * 2**30) if args.workspace_gb else 200 * 2**30
+    with S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec, workspace_bytes=ws,
+                      algorithm=algo) as s:
+        _, t_init = timed(lambda: s.init(At))
+        timed(lambda: s.sweeps(1))
+        _, t_sweep = timed(lambda: s.sweeps(1))
+        e, t_energy = timed(lambda: s.energy(h_nn, h_diag))
+        print(json.dumps({"workload": desc, "algorithm": args.algorithm, "precision": prec,
+                          "init_ms": t_init, "ms_per_move": t_sweep / 4, "energy_ms": t_energy,
+                          "energy_per_site": e, "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}))
     return 0
 
 
