@@ -64,3 +64,19 @@ def test_config_struct_matches_header():
         names = decl.split(None, 1)[1]   # drop the type
         fields += [n.strip().lstrip("*") for n in names.split(",")]
     assert [f for f, _ in S.Config._fields_] == fields
+
+
+def test_missing_library_fails_loudly():
+    """Without the built library the binding raises: there is no CPU fallback."""
+    import subprocess
+    import sys
+    code = ("import paper_2502_10298_gb300.api as a\n"
+            "try:\n"
+            "    a.load_library('/nonexistent/libsplitctmrg.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "else:\n"
+            "    print('no error')\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("raised:") and "not found" in out.stdout, out.stdout
