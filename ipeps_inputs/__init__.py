@@ -16,7 +16,7 @@ import numpy as np
 
 __all__ = [
     "random_cell", "neel_biased_cell", "config", "WORKLOADS",
-    "pauli", "heisenberg_bond", "heisenberg_bond_rotated",
+    "pauli", "heisenberg_bond", "heisenberg_bond_rotated", "honeycomb_bond",
     "product_state_cell", "plaquette_cell", "dimer_cell", "dimer_pairs_cell",
     "gauge_transform_cell", "rotate_cell_90",
 ]
@@ -107,6 +107,28 @@ def heisenberg_bond_rotated(J: float = 1.0) -> np.ndarray:
     _, X, iY, Z = pauli()
     h = 0.25 * (-np.kron(X, X) - np.kron(iY, iY) - np.kron(Z, Z))
     return J * h
+
+
+def honeycomb_bond(J: float = 1.0) -> np.ndarray:
+    """Bond operator of the honeycomb Heisenberg model coarse-grained to the
+    square lattice: every square-lattice site holds the two spins A and B of one
+    honeycomb bond (physical dimension p = 4, index 2 a + b for spins a of A and
+    b of B), and the other two honeycomb bonds of each spin connect B of a site
+    to A of its right neighbour and to A of the neighbour below.  Both square
+    bonds are then h = J S_B(first) . S_A(second), first = left or top site.  The
+    intra-site term J S_A . S_B is shared out over the four bonds of each site,
+    a quarter per bond end, so that the one-operator 2x2-patch energy gives
+    <S_A.S_B> + <horizontal> + <vertical> per square site.  Real 16 x 16 matrix,
+    rows (t_1, t_2), cols (s_1, s_2) as for ``heisenberg_bond``.
+    """
+    I2, X, iY, Z = pauli()
+    I4 = np.eye(4)
+    A_ops = [np.kron(X, I2), np.kron(iY, I2), np.kron(Z, I2)]    # spin A of a site (times 2)
+    B_ops = [np.kron(I2, X), np.kron(I2, iY), np.kron(I2, Z)]    # spin B of a site (times 2)
+    sign = [1.0, -1.0, 1.0]                                      # sigma^y sigma^y = -(iY)(iY)
+    inter = 0.25 * sum(sg * np.kron(b, a) for sg, b, a in zip(sign, B_ops, A_ops))
+    intra = 0.25 * sum(sg * a @ b for sg, a, b in zip(sign, A_ops, B_ops))   # S_A . S_B on one site
+    return J * (inter + 0.25 * (np.kron(intra, I4) + np.kron(I4, intra)))
 
 
 # ------------------------------------------------- exactly solvable test states

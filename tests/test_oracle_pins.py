@@ -321,6 +321,31 @@ def test_implicit_gradient_refuses_a_gauge_that_is_not_fixed():
         implicit_energy_grad(A, 8, HR, split=False, max_sweeps=40)
 
 
+def test_honeycomb_bond_closed_forms():
+    """The coarse-grained honeycomb bond (p = 4: spins A, B of one honeycomb bond
+    per site) on D=1 product states: intra-site singlets give -3/4 per site
+    (singlet -3/4, inter-site bonds 0), Neel A-up B-down gives 3 x (-1/4), and a
+    ferromagnet 3 x (+1/4).  A 1x2 cell fixes the orientation: the horizontal
+    bond couples B of the left site to A of the right site."""
+    h = I.honeycomb_bond()
+
+    def energy(phis, **kw):
+        phis = np.asarray(phis, dtype=np.float64)
+        A = np.zeros(phis.shape[:2] + (4, 1, 1, 1, 1))
+        A[:, :, :, 0, 0, 0, 0] = phis
+        Ac = C.as_cell(A)
+        return En.energy_per_site(Ac, C.split_ctmrg(Ac, 2, 2), h, **kw)
+
+    r = 2 ** -0.5
+    assert abs(float(energy([[[0, r, -r, 0]]])) + 0.75) < 1e-12
+    assert abs(float(energy([[[0, 1, 0, 0]]])) + 0.75) < 1e-12
+    assert abs(float(energy([[[0.5, 0.5, 0.5, 0.5]]])) - 0.75) < 1e-12
+    # left site A-up B-up (index 0), right site A-down B-up (index 2): S_B(left).S_A(right) = -1/4,
+    # and the two intra-site shares (+1/4 and -1/4, a quarter each) cancel
+    _, bonds = energy([[[1, 0, 0, 0], [0, 0, 1, 0]]], return_bonds=True)
+    assert abs(float(bonds[(0, 0)]["top"]) + 0.25) < 1e-12
+
+
 def test_rotation_and_gauge_invariance():
     """The energy of an isotropic Hamiltonian does not change when the lattice
     is rotated by 90 degrees or when gauge matrices are put on every bond
