@@ -179,20 +179,22 @@ def dimer_cell(D: int = 2) -> np.ndarray:
 def dimer_pairs_cell(psis: np.ndarray, D: int = 2, vertical: bool = False) -> np.ndarray:
     """2x2 cell of generic two-site states on the bonds (x,0)-(x,1) (or (0,y)-(1,y)).
 
-    ``psis[k]`` is a (2,2) amplitude matrix psi[s_first, s_second] for row k
-    (column k when vertical).  The first site copies its spin along the bond,
-    the second holds psi; all other bonds carry index 0 only.
+    ``psis[k]`` is a (p,p) amplitude matrix psi[s_first, s_second] for row k
+    (column k when vertical).  The first site copies its state along the bond,
+    the second holds psi; all other bonds carry index 0 only.  Needs D >= p.
     """
-    A = np.zeros((2, 2, 2, D, D, D, D))
+    p = np.asarray(psis).shape[1]
+    assert D >= p
+    A = np.zeros((2, 2, p, D, D, D, D))
     for k in range(2):
-        for s in range(2):
+        for s in range(p):
             if not vertical:
                 A[k, 0, s, 0, 0, 0, s] = 1.0
-                for a in range(2):
+                for a in range(p):
                     A[k, 1, s, 0, a, 0, 0] = psis[k][a, s]
             else:
                 A[0, k, s, 0, 0, s, 0] = 1.0
-                for a in range(2):
+                for a in range(p):
                     A[1, k, s, a, 0, 0, 0] = psis[k][a, s]
     return A
 

@@ -346,6 +346,18 @@ def test_honeycomb_bond_closed_forms():
     assert abs(float(bonds[(0, 0)]["top"]) + 0.25) < 1e-12
 
 
+@pytest.mark.parametrize("vertical", [False, True])
+def test_p4_dimer_states_exact(vertical):
+    """The paper's p = 4 sites (coarse-grained honeycomb bond, R13): a product of
+    generic entangled two-site states (16 amplitudes each, gauge-scrambled
+    bonds) gives the state-vector energy exactly."""
+    h = I.honeycomb_bond()
+    psis = np.random.default_rng(4).standard_normal((2, 4, 4))
+    A = I.gauge_transform_cell(I.dimer_pairs_cell(psis, D=4, vertical=vertical), seed=3)
+    ref = SV.dimer_pairs_energy(psis, h, None, vertical=vertical)
+    assert abs(E_split(A, chi=16, sweeps=3, h=h) - ref) < 1e-12
+
+
 def test_rotation_and_gauge_invariance():
     """The energy of an isotropic Hamiltonian does not change when the lattice
     is rotated by 90 degrees or when gauge matrices are put on every bond
