@@ -271,6 +271,8 @@ def main():
                          "and report the peak device workspace, for workloads whose gradient does not fit")
     ap.add_argument("--chi", type=int, default=128, help="environment dimension of --move-scaling")
     ap.add_argument("--Ds", default="4,5,6,7,8", help="comma-separated bulk dimensions of --move-scaling")
+    ap.add_argument("--p", type=int, default=2,
+                    help="physical dimension of --move-scaling (4: the paper's coarse-grained honeycomb sites)")
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
                     help="time one kernel alone instead of the evaluation (profiling aid)")
     ap.add_argument("--workspace-gb", type=float, default=None)
@@ -282,7 +284,7 @@ def main():
     if args.forward:
         return run_forward(args)
     if args.move_scaling:
-        return run_move_scaling(args, chi=args.chi, Ds=tuple(int(d) for d in args.Ds.split(",")))
+        return run_move_scaling(args, chi=args.chi, Ds=tuple(int(d) for d in args.Ds.split(",")), p=args.p)
 
     import torch
     import paper_2502_10298_gb300 as S
@@ -447,7 +449,7 @@ def run_forward(args):
     return 0
 
 
-def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8)):
+def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8), p=2):
     """Device time of one directional move (mean over a sweep of four, after one
     warm-up sweep) for the split and the conventional CTMRG at fixed chi, 1x1
     cell, seeded N(0,1) tensor, mixed precision: the shape of the paper's
@@ -456,13 +458,13 @@ def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8)):
     import paper_2502_10298_gb300 as S
     rows = []
     for D in Ds:
-        A = I.random_cell(1, 1, 2, D, seed=0)
+        A = I.random_cell(1, 1, p, D, seed=0)
         At = torch.tensor(A, device="cuda")
-        row = {"D": D, "chi": chi}
+        row = {"D": D, "chi": chi, "p": p}
         for name, algo in (("split", 0), ("conventional", 1)):
             n = chi * D * D
             ws = int(min(200 * 2**30, max(8 * 2**30, 40 * n * n * 8)))
-            with S.SplitCTMRG(1, 1, 2, D, chi, precision=1, workspace_bytes=ws, algorithm=algo) as s:
+            with S.SplitCTMRG(1, 1, p, D, chi, precision=1, workspace_bytes=ws, algorithm=algo) as s:
                 s.init(At)
                 s.sweeps(1)
                 torch.cuda.synchronize()
