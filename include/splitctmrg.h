@@ -138,13 +138,19 @@ SCTM_API int split_ctmrg_run(sctm_handle h, int max_sweeps, double tol, int* swe
 SCTM_API int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P_up_dev, double* P_dn_dev,
                      double* s_host);
 
-/* Energy per site from 2x2 patches: (1/N) sum over patch anchors of half of the
- * four nearest-neighbour bond values plus both diagonal bond values.
+/* Energy per site from 2x2 patches of the environment: the expectation value of
+ * the Hamiltonian that Sec. III reads off the (split or conventional) CTMRG
+ * environment, here of a two-site bond operator on the square lattice.
+ * (1/N) sum over patch anchors of half of the four nearest-neighbour bond
+ * values plus both diagonal bond values; each bond value is Tr(rho h)/Tr(rho)
+ * with rho the two-site reduced density matrix of the patch.
  * h_nn_host: p^2 x p^2 nearest-neighbour operator; h_diag_host: diagonal
  * operator or NULL.  Synchronises and writes *e_per_site (host). */
 SCTM_API int energy_2x2(sctm_handle h, const double* h_nn_host, const double* h_diag_host, double* e_per_site);
 
-/* Energy and its gradient with respect to A_cell: initial environment,
+/* Energy and its gradient with respect to A_cell: the variational gradient of
+ * Sec. III, obtained by reverse-mode differentiation through the CTMRG at the
+ * cost of the CTMRG itself (Sec. I, Sec. III).  Initial environment,
  * `sweeps` full steps, 2x2 energy, then the reverse pass through all of it
  * (one environment checkpoint per directional move, each move recomputed with
  * hand-written adjoints; SVD adjoint with Lorentzian broadening; the energy is
@@ -153,11 +159,17 @@ SCTM_API int energy_2x2(sctm_handle h, const double* h_nn_host, const double* h_
 SCTM_API int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const double* h_nn_host,
                 const double* h_diag_host, double* e_per_site, double* grad_dev);
 
-/* Same with host buffers: copies A_cell_host in and the gradient out. */
+/* The energy and gradient of energy_grad (Sec. III) with host buffers: copies
+ * A_cell_host (layout of A_cell, caller-owned host memory) to the device, runs
+ * energy_grad, and copies the gradient into grad_host (same layout, caller-
+ * owned).  Synchronises; errors as energy_grad, plus SCTM_ERR_CUDA for a
+ * failed copy. */
 SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const double* h_nn_host,
                      const double* h_diag_host, double* e_per_site, double* grad_host);
 
-/* Environment of site (x, y) into out_dev, packed in the order C1 T1k T1b C2
+/* Environment of site (x, y) (the split environment of Fig. 2, Sec. II.B; for
+ * the conventional algorithm the environment of Fig. 1, Sec. II.A) into
+ * out_dev (device, caller-owned), packed in the order C1 T1k T1b C2
  * T2k T2b C3 T3b T3k C4 T4b T4k (chi^2 or chi*D*chi doubles each); for the
  * conventional algorithm C1 T1 C2 T2 C3 T3 C4 T4 (chi^2 or chi*D*D*chi each). */
 SCTM_API int sctm_get_env(sctm_handle h, int x, int y, double* out_dev);
@@ -172,11 +184,10 @@ SCTM_API int sctm_svd(sctm_handle h, int m, int n, const double* M_dev, double* 
 
 /* The Jacobi SVD of sctm_svd without a handle and without any allocation.
  * The paper has no counterpart: this entry point exists for callers that
- * must not allocate device memory while they run -- inside a region where
- * allocation is forbidden or unsafe (work being captured into a CUDA graph on
- * their stream, an allocator callback, a loop with a fixed memory budget) --
- * and that hold no engine handle.  Its scratch is one statically sized device
- * array per device (16 MiB + 8 KiB), so:
+ * must not allocate device memory while they run -- code running inside an
+ * allocator callback, or a loop held to a fixed memory budget -- and that hold
+ * no engine handle.  Its scratch is one statically sized device array per
+ * device (16 MiB + 8 KiB), so:
  *  - sizes are limited to (m + n) * n <= 2^21 (e.g. m = n = 1024); larger
  *    matrices return SCTM_ERR_ARG without touching the device;
  *  - calls that overlap in time on one device (two streams, two host threads)
@@ -184,8 +195,9 @@ SCTM_API int sctm_svd(sctm_handle h, int m, int n, const double* M_dev, double* 
  *  - the first call on each device looks up the array's address and the
  *    kernel's occupancy; make it before any stream capture begins.
  * Arguments as for sctm_svd (m >= n, device buffers owned by the caller);
- * stream is a cudaStream_t (NULL = legacy default stream).  The call
- * synchronises that stream and returns SCTM_OK, SCTM_ERR_ARG, SCTM_ERR_CUDA or
+ * stream is a cudaStream_t (NULL = legacy default stream).  The call reads the
+ * kernel's status word back and synchronises that stream before it returns
+ * SCTM_OK, SCTM_ERR_ARG, SCTM_ERR_CUDA or
  * SCTM_ERR_SVD_NOCONV (sweep limit reached).  With sctm_profile recording,
  * the launch is timed with events like every other launch. */
 SCTM_API int sctm_svd_noalloc(int m, int n, const double* M_dev, double* U_dev, double* S_dev, double* V_dev,

@@ -25,7 +25,7 @@ i.e. every tensor is [previous, PEPS leg, next] along the clockwise chain
 C1 T1k T1b C2 T2k T2b C3 T3b T3k C4 T4b T4k.  Environment tensors are stored per
 site ``env[x][y]`` (x row, y column); the left move writes column y+1 from column y.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent (shared with the CUDA path):
 
 * initial environment: double-layer corners/edges of the neighbouring A, edges
   split into ket/bra halves by an SVD truncated to chi_I;
@@ -98,11 +98,16 @@ def projector_pair(rhoT: torch.Tensor, rhoB: torch.Tensor, chi: int,
     a QR decomposition (App. A: decompose rho^T and rho^B before multiplying):
     rhoT^T = Q_T R_T, rhoB = Q_B R_B, K = R_B R_T^T = U' S V'^T; then
     P_up = S^{-1/2} U'^T R_B and P_dn = R_T^T V' S^{-1/2}, which equals the
-    unreduced formula because U = Q_B U', V = Q_T V'.
+    unreduced formula because U = Q_B U', V = Q_T V'.  The reduction is used
+    for values only: when a gradient is being recorded the projectors are
+    formed from M = rhoB rhoT itself (Sec. II.B), because the reverse rule of
+    QR divides by the pivots of R and is undefined when a half is
+    rank-deficient (a truncated environment usually makes it so).
     Returns (P_up, P_dn, s_kept).
     """
     na, nb = rhoT.shape
-    if na < nb:
+    taped = torch.is_grad_enabled() and (rhoT.requires_grad or rhoB.requires_grad)
+    if na < nb and not taped:
         _, RT = torch.linalg.qr(rhoT.T, mode="reduced")      # (alpha, alpha)
         _, RB = torch.linalg.qr(rhoB, mode="reduced")        # (alpha, alpha)
         left, right = RB, RT.T                               # K = RB @ RT^T

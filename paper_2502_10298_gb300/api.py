@@ -236,15 +236,17 @@ def sctm_einsum(h, spec: str, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor 
 def sctm_svd_noalloc(M: torch.Tensor, U=None, S=None, V=None):
     """(U, S, V) of a CUDA float64 matrix (rows >= columns, (m + n) n <= 2^21)
     through the handle-free entry point that allocates no device memory; the
-    output buffers may be passed in (e.g. preallocated before a capture)."""
+    output buffers may be passed in (allocated beforehand by the caller)."""
     load_library()
     m, n = M.shape
     assert M.is_contiguous()
     U = torch.empty((m, n), dtype=torch.float64, device=M.device) if U is None else U
     S = torch.empty((n,), dtype=torch.float64, device=M.device) if S is None else S
     V = torch.empty((n, n), dtype=torch.float64, device=M.device) if V is None else V
-    rc = _lib.sctm_svd_noalloc(m, n, _dev(M), _dev(U), _dev(S), _dev(V),
-                               ctypes.c_void_p(torch.cuda.current_stream(M.device).cuda_stream))
+    # the library takes the scratch of the current device: make M's device current
+    with torch.cuda.device(M.device):
+        rc = _lib.sctm_svd_noalloc(m, n, _dev(M), _dev(U), _dev(S), _dev(V),
+                                   ctypes.c_void_p(torch.cuda.current_stream(M.device).cuda_stream))
     if rc != 0:
         raise SctmError(rc, "sctm_svd_noalloc failed")
     return U, S, V

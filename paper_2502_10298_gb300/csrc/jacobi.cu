@@ -10,6 +10,7 @@
 //
 // One CTA owns one matrix of the batch.  Small matrices (n <= kSmemN) live in
 // shared memory; larger ones in a global workspace (kept in L2).
+#include <mutex>
 #include <algorithm>
 #include <cstdio>
 #include <cooperative_groups.h>
@@ -308,6 +309,8 @@ svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* _
   }
 }
 
+constexpr int kMaxDevices = 64;
+
 static bool fits_smem(int m, int n) { return (long long)(m + n) * n * 8 <= 40 * 1024; }
 
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V, double* work,
@@ -323,14 +326,22 @@ void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, 
   const int in_smem = fits_smem(m, n);
   size_t smem = in_smem ? (size_t)(m + n) * n * sizeof(double) : 0;
   if (!in_smem) {
-    // cooperative multi-CTA path; grid limited to co-resident CTAs
-    static int max_ctas = 0;
-    if (!max_ctas) {
-      int dev = 0, sms = 0, per_sm = 0;
-      SCTM_CUDA(cudaGetDevice(&dev));
-      SCTM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      SCTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_coop_kernel, kCoopThreads, 0));
-      max_ctas = sms * (per_sm > 0 ? per_sm : 1);
+    // cooperative multi-CTA path; grid limited to the co-resident CTAs of the
+    // current device (looked up once per device ordinal, under a lock)
+    static std::mutex mu;
+    static int max_ctas_of[kMaxDevices] = {0};
+    int dev = 0, max_ctas = 0;
+    SCTM_CUDA(cudaGetDevice(&dev));
+    SCTM_CHECK(dev >= 0 && dev < kMaxDevices, "device ordinal out of range");
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      if (!max_ctas_of[dev]) {
+        int sms = 0, per_sm = 0;
+        SCTM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SCTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_coop_kernel, kCoopThreads, 0));
+        max_ctas_of[dev] = sms * (per_sm > 0 ? per_sm : 1);
+      }
+      max_ctas = max_ctas_of[dev];
     }
     long long tasks = (long long)batch * ((n + 1) / 2);
     long long want = (tasks * 32 + kCoopThreads - 1) / kCoopThreads;

@@ -1,11 +1,11 @@
 // One-sided Jacobi SVD entry point that allocates nothing (sctm_svd_noalloc).
 //
-// For callers that cannot allocate device memory while they run -- code inside
-// a region where allocation is forbidden or unsafe (a CUDA graph being
-// captured on their stream, an allocator callback, a real-time loop with a
-// fixed memory budget) -- and that have no engine handle.  The scratch of the
-// multi-CTA Jacobi kernel lives in one file-scope device array per device, so
-// calls that overlap in time (two streams, two host threads) race on it.
+// For callers that cannot allocate device memory while they run -- code
+// inside an allocator callback, or a loop held to a fixed memory budget -- and
+// that have no engine handle.  The scratch of the multi-CTA Jacobi kernel lives
+// in one file-scope device array per device, so calls that overlap in time
+// (two streams, two host threads) race on it.  Every call copies the kernel's
+// status word to the host and synchronises its stream before returning.
 #include <mutex>
 
 #include "../../include/splitctmrg.h"

@@ -434,3 +434,36 @@ def test_oracle_gradient_matches_finite_differences():
         fd = (energy(A0 + h * v) - energy(A0 - h * v)) / (2 * h)
         ad = (g * v).sum()
         assert abs(float(ad) - float(fd)) < 1e-6 * max(1e-3, abs(float(fd)))
+
+
+def test_projector_pair_reduced_and_plain_forms_agree_on_rank_deficient_halves():
+    """App. A's QR reduction (value-only runs) and the plain M = rhoB rhoT form
+    (used when differentiating) give the same projectors; at rank-deficient
+    halves the plain form's gradient is finite and matches a central
+    difference (the kept values are separated from the zero ones)."""
+    rng = np.random.default_rng(7)
+    na, nb, rank, k = 12, 30, 7, 5
+    X = torch.tensor(rng.standard_normal((na, rank)) @ rng.standard_normal((rank, nb)))
+    Y = torch.tensor(rng.standard_normal((nb, rank)) @ rng.standard_normal((rank, na)))
+    with torch.no_grad():
+        up_r, dn_r, s_r = C.projector_pair(X, Y, k)
+    Xg, Yg = X.clone().requires_grad_(True), Y.clone().requires_grad_(True)
+    up_p, dn_p, s_p = C.projector_pair(Xg, Yg, k)
+    assert torch.allclose(s_r[:k], s_p[:k].detach(), rtol=1e-12)
+    # the kept product P_dn P_up is basis independent; P_up rows carry fixed signs
+    assert torch.allclose(dn_r @ up_r, (dn_p @ up_p).detach(), atol=1e-10)
+    assert torch.allclose(up_r, up_p.detach(), atol=1e-10)
+    W = torch.tensor(rng.standard_normal((na, na)))
+    f = ((dn_p @ up_p) * W).sum()
+    f.backward()
+    assert torch.isfinite(Xg.grad).all() and torch.isfinite(Yg.grad).all()
+    dX, dY = torch.tensor(rng.standard_normal(X.shape)), torch.tensor(rng.standard_normal(Y.shape))
+    h = 1e-6
+
+    def fval(t):
+        with torch.no_grad():
+            u, d, _ = C.projector_pair(X + t * dX, Y + t * dY, k)
+            return float(((d @ u) * W).sum())
+    fd = (fval(h) - fval(-h)) / (2 * h)
+    an = float((Xg.grad * dX).sum() + (Yg.grad * dY).sum())
+    assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (fd, an)

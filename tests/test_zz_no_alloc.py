@@ -1,7 +1,9 @@
 """Handle-free SVD entry point without allocation (sctm_svd_noalloc) against
 the handle's sctm_svd: two calls in a row on each path give the same
-decomposition (same kernel, different scratch).  Collected last so it also runs
-after every other GPU test in the same process."""
+decomposition (same kernel, different scratch).  This file sorts after every
+other test file, so a run that stops at the first failure has run all the
+others before it, and the entry point is exercised after them in the same
+process."""
 import numpy as np
 import pytest
 
