@@ -47,7 +47,7 @@ def workload(name, sweeps):
         h_nn = I.heisenberg_bond()
         h_diag = c["J2"] * I.heisenberg_bond() if c["J2"] else None
     if sweeps is None:
-        sweeps = c["bench_sweeps"]
+        sweeps = c["sweeps"]
     desc = (f"{name}: {c['Lx']}x{c['Ly']} cell, d={c['p']}, D={c['D']}, chi={c['chi']}, "
             f"{'rotated ' if c['rotated'] else ''}Heisenberg J1=1" + (f", J2={c['J2']}" if c["J2"] else "")
             + f", {sweeps} directional sweeps per evaluation")
@@ -105,9 +105,46 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+CPU_WORKLOAD, CPU_SWEEPS = "d4_chi32_2x2", 2
+
+
+def oracle_evaluation(name=CPU_WORKLOAD, sweeps=CPU_SWEEPS):
+    """One whole energy+gradient evaluation of the FP64 oracle (initial
+    environment, `sweeps` full steps, 2x2 energy, reverse-mode autograd) on the
+    host cores, timed; returns (seconds, energy, threads)."""
+    import torch
+    from oracle import ctmrg as C
+    from oracle import energy as En
+    torch.set_num_threads(os.cpu_count() or 1)
+    A, c, h_nn, h_diag, _, _ = workload(name, sweeps)
+    t0 = time.perf_counter()
+    Ao = torch.tensor(A).requires_grad_(True)
+    Ac = [[Ao[x, y] for y in range(c["Ly"])] for x in range(c["Lx"])]
+    e = En.energy_per_site(Ac, C.split_ctmrg(Ac, c["chi"], sweeps), h_nn, h_diag)
+    e.backward()
+    return time.perf_counter() - t0, float(e.detach()), torch.get_num_threads()
+
+
 def cpu_baseline(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
-    """Time the FP64 oracle on a bounded sample of the same workload and scale
-    it to one energy+gradient evaluation.
+    """The FP64 oracle timed on the host cores: one whole energy+gradient
+    evaluation of the 2x2, D=4, chi=32 workload (2 sweeps), which it finishes
+    in seconds.  The D=8 workload takes the oracle hours per evaluation; its
+    figure is reported beside as an estimate scaled from a bounded sample
+    (``estimate_of``, see d8_estimate), not as a timing."""
+    t, e, threads = oracle_evaluation()
+    est = d8_estimate(name, c, A, h_nn, h_diag, sweeps, budget_s=budget_s)
+    return {"value": 1.0 / t, "unit": "evals/s", "cores": threads, "kind": "oracle",
+            "sample": f"one whole oracle energy+gradient evaluation of {CPU_WORKLOAD} (2x2 cell, d=2, D=4, chi=32, "
+                      f"Heisenberg J=1, {CPU_SWEEPS} sweeps, autograd reverse pass) timed on the host: {t:.2f} s, "
+                      f"E={e:.12f}",
+            "workload": CPU_WORKLOAD, "sweeps": CPU_SWEEPS,
+            "estimate_of": {"workload": name, "value": est["value"], "unit": "evals/s", "kind": "estimate",
+                            "how": est["sample"]}}
+
+
+def d8_estimate(name, c, A, h_nn, h_diag, sweeps, budget_s=20.0):
+    """An ESTIMATE, not a timing: the FP64 oracle timed on a bounded sample of
+    the workload and scaled to one energy+gradient evaluation.
 
     Sample: (1) the oracle's initial environment; (2) single-column projector
     stages of a left move (every colour's rho networks, decompositions and the
@@ -177,6 +214,14 @@ def roofline_of(fam, p, peaks, src, prec):
                 "traffic": None, "kernel": "other (packing, copies, scaling)",
                 "peak_source": f"{src} copy bandwidth"}
     achieved = p["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    if fam == "tensor" and prec == 4:
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "slice_gemm_kernel (BF16 digit-slice tcgen05 contraction)",
+                "peak_source": f"{src} bf16 sustained",
+                "tensor_pipe_frac": 10.0 * achieved / peak,
+                "note": "achieved counts 2MNK; the pipe executes ten BF16 products per multiply-add"}
     if fam == "tensor":
         bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         peak = bf16 * 1.1 / 2.25
@@ -215,28 +260,38 @@ def aggregate_over_ranks(total_ms, steps, world, dist, device):
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, on this arm's workload and metric.
+    One evaluation at D=8, chi=128 takes the oracle hours, so each of the W + K
+    steps times a bounded sample of it (the initial environment, one column
+    stage of a left move, one closed-corner product of the energy) and scales
+    it to one evaluation: ``value`` is that estimate, labelled as such, and
+    ``ms_per_step`` the measured wall time of a sample step.  One whole oracle
+    evaluation of the small 2x2, D=4, chi=32 workload is timed beside it."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
     prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
-    # W untimed and K timed steps, each one bounded sample of the workload (one
-    # column stage when there are several steps, so that the run stays within minutes)
     steps = max(1, args.steps)
     budget = args.cpu_budget if args.warmup + steps == 1 else 0.0
-    timed = []
+    timed, wall = [], 0.0
     for i in range(args.warmup + steps):
-        s = cpu_baseline(args.config, c, A, h_nn, h_diag, sweeps, budget_s=budget)
+        t0 = time.perf_counter()
+        est = d8_estimate(args.config, c, A, h_nn, h_diag, sweeps, budget_s=budget)
         if i >= args.warmup:
-            timed.append(s)
-    t_eval = sum(1.0 / s["value"] for s in timed) / len(timed)
-    cb = dict(timed[-1])
-    cb["value"] = 1.0 / t_eval
-    cb["sample"] = (f"mean of {len(timed)} timed steps after {args.warmup} untimed ones; each step: "
-                    + timed[-1]["sample"])
+            timed.append(est)
+            wall += time.perf_counter() - t0
+    t_eval = sum(1.0 / e["value"] for e in timed) / len(timed)
+    t_small, e_small, threads = oracle_evaluation()
+    cb = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": threads, "kind": "oracle",
+          "value_kind": "estimate scaled from a bounded sample per step",
+          "sample": f"mean of {len(timed)} timed steps after {args.warmup} untimed ones; each step: "
+                    + timed[-1]["sample"],
+          "measured_small": {"workload": CPU_WORKLOAD, "sweeps": CPU_SWEEPS, "value": 1.0 / t_small,
+                             "unit": "evals/s", "kind": "one whole oracle evaluation, timed"}}
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "evals/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / cb["value"],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": arm_config(desc, prec, world),
             "cpu_baseline": cb,
@@ -245,7 +300,15 @@ def run_reference(args):
     return 0
 
 
+DTYPES = {0: "f64", 1: "tf32x3 (f32 accumulate) + f32 + f64", 2: "f32 + f64", 3: "f64",
+          4: "bf16 x4 digit slices (exact f32 level sums) + f32 + f64"}
+
 METRIC = "energy+gradient evals/s (split-CTMRG, D=8 chi=128) & TFLOP/s vs peak, vs FP64"
+
+
+def _cpu_args(args):
+    A, c, h_nn, h_diag, sweeps, _ = workload(args.config, args.sweeps)
+    return c, A, h_nn, h_diag, sweeps, args.cpu_budget
 
 
 def main():
@@ -257,7 +320,8 @@ def main():
     ap.add_argument("--config", default="d8_chi128_2x2_j1j2", choices=sorted(I.WORKLOADS))
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--precision", type=int, default=None,
-                    help="0 FP64, 1 mixed (3xTF32 tensor cores), 2 mixed on CUDA cores; default per workload")
+                    help="0 FP64, 1 mixed (3xTF32 tensor cores), 2 mixed on CUDA cores, 3 FP64 with randomized "
+                         "projectors, 4 mixed with BF16 digit slices on the tensor cores; default per workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -276,7 +340,14 @@ def main():
     ap.add_argument("--kernel", default=None, choices=["corner-product"],
                     help="time one kernel alone instead of the evaluation (profiling aid)")
     ap.add_argument("--workspace-gb", type=float, default=None)
+    ap.add_argument("--precisions", default=None,
+                    help="comma-separated precisions: one evaluation each at equal sweeps and cutoff (the FP64 "
+                         "form beside the mixed ones), precision 0 first for the gradient reference")
+    ap.add_argument("--cutoff", type=float, default=1e-5, help="projector cutoff of --precisions")
+    ap.add_argument("--oracle-energy", action="store_true", help="--precisions: also the oracle's forward energy")
     args = ap.parse_args()
+    if args.precisions:
+        return run_precisions(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel:
@@ -288,6 +359,11 @@ def main():
 
     import torch
     import paper_2502_10298_gb300 as S
+    if not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        # the oracle's thread pool is started before the first GPU call
+        cpu_first = cpu_baseline(args.config, *_cpu_args(args))
+    else:
+        cpu_first = None
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -320,7 +396,6 @@ def main():
         dist.barrier()
     clk = ClockSampler(local)
     clk.start()
-    S.sctm_profile(s.h, True)
     total_ms = 0.0
     e_val = None
     for _ in range(args.steps):
@@ -332,10 +407,19 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         total_ms += ev0.elapsed_time(ev1)
-    prof = S.sctm_profile(s.h, False)
     clocks = clk.stop()
     torch.cuda.synchronize()
     ms_per_step, value = aggregate_over_ranks(total_ms, args.steps, world, dist, "cuda")
+    # how converged the environment of the evaluation is: one more full step from
+    # it, and the change of the normalised corner spectra (split_ctmrg_run's measure)
+    _, conv_delta = S.split_ctmrg_run(s.h, 1)
+    # per-family breakdown from one extra, untimed step with the engine's event profiler
+    flush.zero_()
+    torch.cuda.synchronize()
+    S.sctm_profile(s.h, True)
+    step()
+    prof = S.sctm_profile(s.h, False)
+    prof_steps = 1
 
     # end-to-end through the host-buffer C-ABI call (H2D of A, D2H of grad + energy inside the timing)
     e2e = None
@@ -354,7 +438,7 @@ def main():
 
     peaks, src = load_peaks()
     tot_ms = sum(v["ms"] for v in prof.values())
-    fams = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+    fams = {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                 "share_of_device_time": v["ms"] / tot_ms if tot_ms else None,
                 "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else 0.0}
             for k, v in prof.items()}
@@ -364,15 +448,28 @@ def main():
     roof["share_of_device_time"] = p["ms"] / tot_ms if tot_ms else None
     roof["families"] = fams
     cpu = None
-    if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline(args.config, c, A, h_nn, h_diag, sweeps, budget_s=args.cpu_budget)
-    launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
+    if cpu_first is not None and rank == 0:
+        cpu = cpu_first
+        # the GPU on the same small evaluation the oracle was timed on
+        Ac_, cc_, hn_, hd_, sw_, _ = workload(CPU_WORKLOAD, CPU_SWEEPS)
+        At_ = torch.tensor(Ac_, device="cuda")
+        with S.SplitCTMRG(cc_["Lx"], cc_["Ly"], cc_["p"], cc_["D"], cc_["chi"], precision=prec) as s2:
+            s2.energy_grad(At_, sw_, hn_, hd_)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                s2.energy_grad(At_, sw_, hn_, hd_)
+            torch.cuda.synchronize()
+            cpu["gpu_same_workload"] = {"value": 3.0 / (time.perf_counter() - t0), "unit": "evals/s",
+                                        "precision": prec}
+    launches = int(sum(v["launches"] for v in prof.values()) / prof_steps)
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f64", 1: "tf32x3 (f32 accumulate) + f64", 2: "f32 + f64", 3: "f64"}[prec],
+            "vs_baseline": None, "dtype": DTYPES[prec],
             "data": "synthetic",
             "config": arm_config(desc, prec, world),
-            "energy_per_site": e_val, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+            "energy_per_site": e_val, "convergence_delta": conv_delta, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu,
             "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
     s.close()
@@ -385,13 +482,15 @@ def main():
 
 def run_kernel(args):
     """One enlarged-corner product of the 2x2 energy, (chi D^2)^3 = 8192^3 at the
-    D=8, chi=128 workload, through sctm_einsum on the tensor cores: the dominant
-    kernel of an evaluation, timed alone (burst) with CUDA events."""
+    D=8, chi=128 workload, through sctm_einsum on the tensor cores (precision 1:
+    3xTF32; precision 4: BF16 digit slices): the dominant kernel of an
+    evaluation, timed alone (burst) with CUDA events."""
     import torch
     import paper_2502_10298_gb300 as S
     A, c = I.config(args.config)
     n = c["chi"] * c["D"] ** 2
-    h = S.sctm_create(1, 1, 2, 2, 4, precision=1, workspace_bytes=int(2 * 16 * n * n + (1 << 30)))
+    prec = args.precision if args.precision is not None else 1
+    h = S.sctm_create(1, 1, 2, 2, 4, precision=prec, workspace_bytes=int(2 * 16 * n * n + (1 << 30)))
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
     Y = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
@@ -406,13 +505,17 @@ def run_kernel(args):
     S.sctm_destroy(h)
     t = prof["tensor"]
     peaks, src = load_peaks()
-    peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
     ach = t["flops"] / (t["ms"] * 1e-3) / 1e12
-    print(json.dumps({"kernel": "tc_gemm_kernel", "shape": [n, n, n], "launches": t["launches"],
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    if prec == 4:
+        kern, peak, products, psrc = "slice_gemm_kernel", bf16, 10, f"{src} bf16 burst"
+    else:
+        kern, peak, products, psrc = "tc_gemm_kernel", bf16 * 1.1 / 2.25, 3, f"{src} bf16 burst x 1.1/2.25"
+    print(json.dumps({"kernel": kern, "precision": prec, "shape": [n, n, n], "launches": t["launches"],
                       "ms_per_launch": t["ms"] / max(1, t["launches"]), "achieved_tflops": ach,
-                      "peak_tf32_tflops": peak, "frac": ach / peak, "tensor_pipe_frac": 3 * ach / peak,
+                      "peak_tflops": peak, "frac": ach / peak, "tensor_pipe_frac": products * ach / peak,
                       "pack_ms_per_step": prof["other"]["ms"] / max(1, args.steps),
-                      "peak_source": f"{src} bf16 burst x 1.1/2.25"}))
+                      "peak_source": psrc}))
     return 0
 
 
@@ -476,6 +579,57 @@ def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8), p=2):
                 row[name + "_ms_per_move"] = ev0.elapsed_time(ev1) / 4
         rows.append(row)
         print(json.dumps(row), flush=True)
+    return 0
+
+
+def run_precisions(args):
+    """The plain FP64 form beside the mixed forms at equal sweeps and cutoff:
+    one timed energy+gradient evaluation per precision (after a warm-up of the
+    kernels on a small cell), its energy against the FP64 oracle's forward pass
+    (same sweeps and cutoff) and its gradient against the FP64 GPU form's
+    (precision 0, which matches the oracle's autograd to 1e-10 where that runs).
+    One JSON line per precision."""
+    import torch
+    import paper_2502_10298_gb300 as S
+    from oracle import ctmrg as C
+    from oracle import energy as En
+    S.load_library()
+    A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
+    cut = args.cutoff
+    precs = [int(x) for x in args.precisions.split(",")]
+    e_or = None
+    if args.oracle_energy:
+        import torch as T
+        T.set_num_threads(os.cpu_count() or 1)
+        old = C.CUTOFF
+        C.CUTOFF = cut
+        t0 = time.perf_counter()
+        with T.no_grad():
+            Ac = C.as_cell(A)
+            e_or = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, c["chi"], sweeps), h_nn, h_diag))
+        C.CUTOFF = old
+        print(json.dumps({"oracle_energy": e_or, "seconds": time.perf_counter() - t0, "cutoff": cut}), flush=True)
+    At = torch.tensor(A, device="cuda")
+    with S.SplitCTMRG(1, 1, 2, 2, 8, precision=4) as w:   # load and warm every kernel once
+        w.energy_grad(torch.tensor(I.random_cell(1, 1, 2, 2, seed=1), device="cuda"), 1, I.heisenberg_bond())
+    g_ref = None
+    for prec in precs:
+        with S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec, svd_cutoff=cut,
+                          workspace_bytes=args_ws(c, args.workspace_gb)) as s:
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            e, g = s.energy_grad(At, sweeps, h_nn, h_diag)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+        if prec == 0:
+            g_ref = g.clone()
+        line = {"workload": desc, "precision": prec, "dtype": DTYPES[prec], "cutoff": cut, "sweeps": sweeps,
+                "evals_per_s": 1000.0 / ms, "ms": ms, "energy_per_site": e,
+                "energy_err_vs_oracle": (e - e_or) if e_or is not None else None,
+                "grad_rel_err_vs_fp64_gpu": (float((g - g_ref).norm() / g_ref.norm()) if g_ref is not None else None)}
+        print(json.dumps(line), flush=True)
     return 0
 
 

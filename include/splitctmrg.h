@@ -67,7 +67,15 @@ typedef struct {
                                cutoff 1e-5.
                             2: as 1 with every contraction on the CUDA cores (FP32).
                             3: FP64 arithmetic throughout with the randomized
-                               projectors of 1 (cutoff default 1e-6). */
+                               projectors of 1 (cutoff default 1e-6).
+                            4: as 1 with the large contractions on the tcgen05 tensor
+                               cores as BF16 digit slices: every row of A and column
+                               of B scaled by a power of two and split into four BF16
+                               slices of 8 bits, ten BF16 products per multiply-add,
+                               the two leading levels accumulated exactly in FP32
+                               (error-free splitting of Ozaki et al. 2012); about
+                               2^-32 relative to the largest terms, FP64 output.
+                               Default cutoff 1e-5. */
   double svd_cutoff;     /* relative singular-value cutoff of projectors (<=0: 1e-8) */
   double lorentz_eps;    /* Lorentzian broadening of the SVD adjoint (<=0: 1e-36 s_max^4) */
   size_t workspace_bytes;/* device workspace; 0 = library default          */
@@ -92,6 +100,11 @@ typedef struct {
                             [previous, ket leg, bra leg, next] (chi x D x D x chi) and
                             the same calls (init, move, energy_2x2, energy_grad) apply;
                             ctmrg_projectors is not available for it                */
+  int projector_order;   /* split CTMRG: 0 = the physical leg of the ket is truncated
+                            by the red projectors (Sec. II.B, App. A); 1 = by the
+                            yellow ones (the alternative order of App. B, which
+                            removes the p^3 factor of the red decomposition): yellow
+                            then truncates (chi_I, D, p) and red (chi_I, D)         */
 } sctm_config;
 
 /* Create a handle.  stream: a cudaStream_t (NULL = legacy default stream). */
@@ -133,8 +146,9 @@ SCTM_API int split_ctmrg_run(sctm_handle h, int max_sweeps, double tol, int* swe
  * without moving.  colour: 0 green, 1 teal, 2 yellow, 3 red (Sec. II.B, App. A).
  * (x, y) is the site in the frame of the move (the left-move frame is the
  * lattice itself).  P_up_dev: [chi][alpha], P_dn_dev: [alpha][chi] with
- * alpha = chi*D (green, teal, yellow) or chi*p*D (red); s_host receives the
- * chi largest singular values of the decomposed core. */
+ * alpha = chi*D (green, teal; yellow in order 0; red in order 1), chi*p*D
+ * (red in order 0: [chi][p][D]) or chi*D*p (yellow in order 1: [chi][D][p]);
+ * s_host receives the chi largest singular values of the decomposed core. */
 SCTM_API int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P_up_dev, double* P_dn_dev,
                      double* s_host);
 
@@ -223,6 +237,18 @@ SCTM_API int sctm_profile(sctm_handle h, int enable, double* out);
 
 /* Device workspace high-water mark in bytes. */
 SCTM_API int sctm_workspace_high_water(sctm_handle h, size_t* bytes);
+
+/* Limits of the handle's bounded device loops, for fault-injection tests (the
+ * paper has no counterpart).  svd_max_sweeps: sweeps of every Jacobi SVD the
+ * handle runs (<= 0: the default 60); a decomposition that reaches it makes
+ * the call return SCTM_ERR_SVD_NOCONV.  pipeline_wait_s: how long the main
+ * loop of a tensor-core contraction waits on one of its mbarriers before it
+ * gives up (< 0: the default 2 s; 0: at the first wait not already
+ * satisfied); a kernel that gives up waits with the full 2 s limit for the
+ * copies and MMAs it issued, frees its tensor memory, returns, and the call
+ * returns SCTM_ERR_CUDA.  In both cases the handle stays usable: the failed
+ * call is rolled back.  Errors: SCTM_ERR_ARG for pipeline_wait_s > 60. */
+SCTM_API int sctm_set_limits(sctm_handle h, int svd_max_sweeps, double pipeline_wait_s);
 
 #ifdef __cplusplus
 }

@@ -85,7 +85,7 @@ def rescale(t: torch.Tensor) -> torch.Tensor:
 
 
 def projector_pair(rhoT: torch.Tensor, rhoB: torch.Tensor, chi: int,
-                   cutoff: float = CUTOFF, eps_l: float = EPS_L):
+                   cutoff: float = None, eps_l: float = EPS_L):
     """Projector pair from two half networks (Sec. II.B, Fig. 3).
 
     rhoT: (alpha, beta) upper half, rhoB: (beta, alpha) lower half, alpha being
@@ -103,8 +103,10 @@ def projector_pair(rhoT: torch.Tensor, rhoB: torch.Tensor, chi: int,
     formed from M = rhoB rhoT itself (Sec. II.B), because the reverse rule of
     QR divides by the pivots of R and is undefined when a half is
     rank-deficient (a truncated environment usually makes it so).
+    ``cutoff`` defaults to the module's CUTOFF at call time.
     Returns (P_up, P_dn, s_kept).
     """
+    cutoff = CUTOFF if cutoff is None else cutoff
     na, nb = rhoT.shape
     taped = torch.is_grad_enabled() and (rhoT.requires_grad or rhoB.requires_grad)
     if na < nb and not taped:
@@ -155,7 +157,7 @@ def _double_layer_pieces(A):
     return c1, t1, c2, t2, c3, t3, c4, t4
 
 
-def _split_edge(T: torch.Tensor, chi: int, cutoff: float = CUTOFF):
+def _split_edge(T: torch.Tensor, chi: int, cutoff: float = None):
     """Split a conventional edge T[p, k, k', n] into first[p,k,i] second[i,k',n].
 
     SVD of the matrix (p,k) x (k',n), truncated to chi and the cutoff;
@@ -163,6 +165,7 @@ def _split_edge(T: torch.Tensor, chi: int, cutoff: float = CUTOFF):
     entry of every column of U is positive.  The first factor is the tensor that
     comes first along the clockwise chain.
     """
+    cutoff = CUTOFF if cutoff is None else cutoff
     P, K, K2, N = T.shape
     Mt = T.reshape(P * K, K2 * N)
     U, S, Vh = torch.linalg.svd(Mt, full_matrices=False)
@@ -371,7 +374,14 @@ def yellow_rhoB(E, A):
 
 def _upper_left_k(E, A, K):
     """Column y of the upper half after the ket stage: C1k T1b T4k_k T4b_k A'.
-    Legs [r, c, t, e, z]: right (c = T1b.c, r = A.r, z = A'.r'), bottom (t, e = A'.d')."""
+    Legs [r, c, t, e, z]: right (c = T1b.c, r = A.r, z = A'.r'), bottom (t, e = A'.d').
+    The ket's physical leg s is open on T4k_k (standard order) or on T4b_k
+    (alternative order, where yellow truncated it)."""
+    if K["T4kk"].dim() == 3:                                   # alternative order
+        X = es("ig,gry->iry", K["C1k"], K["T4kk"])
+        X = es("iry,iwc->rywc", X, E["T1b"])
+        X = es("rywc,yvts->rwcvts", X, K["T4bk"])
+        return es("rwcvts,swvez->rctez", X, A)
     X = es("ig,grys->irys", K["C1k"], K["T4kk"])
     X = es("irys,iwc->ryswc", X, E["T1b"])
     X = es("ryswc,yvt->rswcvt", X, K["T4bk"])
@@ -394,6 +404,10 @@ def _lower_left_k(E, A, K):
     """Column y of the lower half after the ket stage: T4k_k T4b_k C4k A' T3b.
     Legs [h, w, z, g, r]: top (g = T4k_k.g, w = A'.u'), right (r, z, h = T3b.h)."""
     Z = es("tk,hek->the", K["C4k"], E["T3b"])
+    if K["T4kk"].dim() == 3:                                   # alternative order
+        Z = es("the,yvts->heyvs", Z, K["T4bk"])
+        Z = es("heyvs,swvez->hywz", Z, A)
+        return es("hywz,gry->hwzgr", Z, K["T4kk"])
     Z = es("the,yvt->heyv", Z, K["T4bk"])
     Z = es("heyv,swvez->hyswz", Z, A)
     return es("hyswz,grys->hwzgr", Z, K["T4kk"])
@@ -458,6 +472,110 @@ def red_rhoB(E, A, K, E2, A2):
     return R.reshape(D * S * W_ * j, y * s * w)
 
 
+# ------------------------------ alternative yellow/red order (App. B)
+# App. B proposes to absorb the ket's physical leg into the yellow projectors
+# instead of the red ones, which removes the p^3 factor of the red SVD:
+# yellow then truncates (T4ket.q, A.d, A.s) -> chi_I on the same networks as
+# Fig. 8 with the physical leg moved to the truncated side, and red truncates
+# (yellow chi_I, T1bra.u') -> chi_I.  After the ket stage T4ket_k[g, r, y] has
+# no physical leg and T4bra_k[y, l', g2, s] carries it to the bra layer, which
+# closes it when the bra is absorbed.
+
+def yellow_alt_rhoT(E, A):
+    """rho^T_yellow of the alternative order: the network of yellow_rhoT with
+    open (T4k.q, A.d, A.s | T1b.u', T2k.j) -> (alpha=(q, d, s)) x (beta=(u', j))."""
+    X = es("ab,aui->bui", E["C1"], E["T1k"])
+    X = es("bui,qlb->uiql", X, E["T4k"])
+    X = es("uiql,sulkr->iqskr", X, A)
+    X = es("iqskr,iwc->qskrwc", X, E["T1b"])
+    X = es("qskrwc,cf->qskrwf", X, E["C2"])
+    R = es("qskrwf,frj->qkswj", X, E["T2k"])
+    q, k, s_, w, j = R.shape
+    return R.reshape(q * k * s_, w * j)
+
+
+def yellow_alt_rhoB(E, A):
+    """rho^B_yellow of the alternative order: the network of yellow_rhoB with
+    open (A'.u', T2b.j | T4b.q, T3k.d, A'.s) -> (beta=(u', j)) x (alpha=(q, d, s))."""
+    Y = es("mn,kdm->nkd", E["C4"], E["T3k"])
+    Y = es("nkd,nvq->kdvq", Y, E["T4b"])
+    Y = es("kdvq,hek->dvqhe", Y, E["T3b"])
+    Y = es("dvqhe,gh->dvqeg", Y, E["C3"])
+    Y = es("dvqeg,jzg->dvqejz", Y, E["T2b"])
+    Y = es("dvqejz,swvez->dqjsw", Y, A)
+    R = es("dqjsw->wjqds", Y)
+    w, j, q, d, s_ = R.shape
+    return R.reshape(w * j, q * d * s_)
+
+
+def red_alt_rhoT(E, K, E2, A2):
+    """rho^T_red of the alternative order (two-column reading, as red_rhoT):
+    open (T4k_k.y, T1b.u' | A.d, A.s, T1b.u', T2k.j of column y+1)."""
+    X = es("ig,gry->iry", K["C1k"], K["T4kk"])
+    X = es("iry,iwc->rywc", X, E["T1b"])
+    Y = es("cui,iWC->cuWC", E2["T1k"], E2["T1b"])
+    Y = es("cuWC,Cf->cuWf", Y, E2["C2"])
+    Y = es("cuWf,fRj->cuWRj", Y, E2["T2k"])
+    Y = es("cuWRj,SulDR->cWjSlD", Y, A2)
+    R = es("rywc,cWjSrD->ywDSWj", X, Y)
+    y, w, D, S, W, j = R.shape
+    return R.reshape(y * w, D * S * W * j)
+
+
+def red_alt_rhoB(E, A, K, E2, A2):
+    """rho^B_red of the alternative order: open (T3k.d, A'.s, A'.u', T2b.j of
+    column y+1) x (T4b_k.y, A'.u'); the bra closes the physical leg of T4b_k."""
+    Z = es("tk,hek->the", K["C4k"], E["T3b"])
+    Z = es("the,yvts->heyvs", Z, K["T4bk"])
+    Z = es("heyvs,swvez->hywz", Z, A)
+    W = es("jZG,GH->jZH", E2["T2b"], E2["C3"])
+    W = es("jZH,HEK->jZEK", W, E2["T3b"])
+    W = es("jZEK,KDh->jZEDh", W, E2["T3k"])
+    W = es("jZEDh,SWvEZ->jDhSWv", W, A2)
+    R = es("jDhSWv,hywv->DSWjyw", W, Z)
+    D, S, W_, j, y, w = R.shape
+    return R.reshape(D * S * W_ * j, y * w)
+
+
+def ket_stage_alt(E, A, Pg_above, Py, Pg_below):
+    """Ket stage of the alternative order: as ket_stage, with the yellow pair
+    acting on (q, d, s); T4k_k[g, r, y], T4b_k[y, l', g2, s]."""
+    gu_a, gd_a = Pg_above
+    yu, yd = Py
+    gu_b, gd_b = Pg_below
+    X = es("ab,aui->bui", E["C1"], E["T1k"])
+    C1k = es("bui,gbu->ig", X, gu_a)
+    Z = es("bug,qlb->ugql", gd_a, E["T4k"])
+    Z = es("ugql,suldr->gqsdr", Z, A)
+    T4kk = es("gqsdr,yqds->gry", Z, yu)
+    Z = es("qksy,nvq->ksynv", yd, E["T4b"])
+    T4bk = es("ksynv,tnk->yvts", Z, gu_b)
+    Z = es("mn,kdm->nkd", E["C4"], E["T3k"])
+    C4k = es("nkd,ndt->tk", Z, gd_b)
+    return dict(C1k=C1k, T4kk=T4kk, T4bk=T4bk, C4k=C4k)
+
+
+def bra_stage_alt(E, A, K, Pt_above, Pr, Pt_below):
+    """Bra stage of the alternative order: as bra_stage, with the red pair
+    acting on (y, u') and the bra closing the physical leg of T4b_k."""
+    tu_a, td_a = Pt_above
+    ru, rd = Pr
+    tu_b, td_b = Pt_below
+    X = es("ig,iwc->gwc", K["C1k"], E["T1b"])
+    C1n = es("gwc,Tgw->cT", X, tu_a)
+    Z = es("gwT,gry->Twry", td_a, K["T4kk"])
+    T4kn = es("Twry,Pyw->TrP", Z, ru)
+    Z = es("ywP,yvts->wPvts", rd, K["T4bk"])
+    Z = es("wPvts,swvez->Ptez", Z, A)
+    T4bn = es("Ptez,Ote->PzO", Z, tu_b)
+    Z = es("tk,hek->the", K["C4k"], E["T3b"])
+    C4n = es("the,teO->Oh", Z, td_b)
+    return dict(C1=C1n, T4k=T4kn.permute(2, 1, 0), T4b=T4bn.permute(2, 1, 0), C4=C4n.T)
+
+
+ORDERS = ("standard", "alternative")
+
+
 # ------------------------------------------------------------ split left move
 def ket_stage(E, A, Pg_above, Py, Pg_below):
     """Absorb the ket layer of one site and apply green/yellow projectors.
@@ -505,8 +623,12 @@ def _pair_tensors(Pup, Pdn, shape_alpha):
     return Pup.reshape(k, *shape_alpha), Pdn.reshape(*shape_alpha, k)
 
 
-def split_column_projectors(A, env, y, chi, record=None):
-    """All projectors and ket-stage tensors of one column (left move)."""
+def split_column_projectors(A, env, y, chi, record=None, order="standard"):
+    """All projectors and ket-stage tensors of one column (left move).
+    order: "standard" (the physical leg truncated by red, Sec. II.B) or
+    "alternative" (by yellow, App. B)."""
+    assert order in ORDERS, order
+    alt = order == "alternative"
     Lx, Ly = len(A), len(A[0])
     yp = (y + 1) % Ly
     E = [env[x][y] for x in range(Lx)]
@@ -524,11 +646,16 @@ def split_column_projectors(A, env, y, chi, record=None):
         if record is not None:
             record.setdefault("green", []).append((up, dn, s))
     for x in range(Lx):
-        up, dn, s = projector_pair(yellow_rhoT(E[x], a[x]), yellow_rhoB(E[x], a[x]), chi_i)
-        Py.append(_pair_tensors(up, dn, (E[x]["T4k"].shape[0], D)))
+        if alt:
+            up, dn, s = projector_pair(yellow_alt_rhoT(E[x], a[x]), yellow_alt_rhoB(E[x], a[x]), chi_i)
+            Py.append(_pair_tensors(up, dn, (E[x]["T4k"].shape[0], D, p)))
+        else:
+            up, dn, s = projector_pair(yellow_rhoT(E[x], a[x]), yellow_rhoB(E[x], a[x]), chi_i)
+            Py.append(_pair_tensors(up, dn, (E[x]["T4k"].shape[0], D)))
         if record is not None:
             record.setdefault("yellow", []).append((up, dn, s))
-    K = [ket_stage(E[x], a[x], Pg[(x - 1) % Lx], Py[x], Pg[x]) for x in range(Lx)]
+    stage = ket_stage_alt if alt else ket_stage
+    K = [stage(E[x], a[x], Pg[(x - 1) % Lx], Py[x], Pg[x]) for x in range(Lx)]
     Pt, Pr = [], []
     for x in range(Lx):
         xp = (x + 1) % Lx
@@ -538,15 +665,20 @@ def split_column_projectors(A, env, y, chi, record=None):
         if record is not None:
             record.setdefault("teal", []).append((up, dn, s))
     for x in range(Lx):
-        up, dn, s = projector_pair(red_rhoT(E[x], K[x], E2[x], a2[x]),
-                                   red_rhoB(E[x], a[x], K[x], E2[x], a2[x]), chi_i)
-        Pr.append(_pair_tensors(up, dn, (K[x]["T4kk"].shape[2], p, D)))
+        if alt:
+            up, dn, s = projector_pair(red_alt_rhoT(E[x], K[x], E2[x], a2[x]),
+                                       red_alt_rhoB(E[x], a[x], K[x], E2[x], a2[x]), chi_i)
+            Pr.append(_pair_tensors(up, dn, (K[x]["T4kk"].shape[2], D)))
+        else:
+            up, dn, s = projector_pair(red_rhoT(E[x], K[x], E2[x], a2[x]),
+                                       red_rhoB(E[x], a[x], K[x], E2[x], a2[x]), chi_i)
+            Pr.append(_pair_tensors(up, dn, (K[x]["T4kk"].shape[2], p, D)))
         if record is not None:
             record.setdefault("red", []).append((up, dn, s))
     return E, a, K, Pg, Py, Pt, Pr, E2, a2
 
 
-def split_left_move(A, env, chi, record=None):
+def split_left_move(A, env, chi, record=None, order="standard"):
     """One directional left move over every column of the unit cell.
 
     Column y (in order y = 0..Ly-1) is absorbed into the left environment of
@@ -556,8 +688,9 @@ def split_left_move(A, env, chi, record=None):
     Lx, Ly = len(A), len(A[0])
     env = [list(row) for row in env]
     for y in range(Ly):
-        E, a, K, Pg, Py, Pt, Pr, _, _ = split_column_projectors(A, env, y, chi, record)
-        new = [bra_stage(E[x], a[x], K[x], Pt[(x - 1) % Lx], Pr[x], Pt[x]) for x in range(Lx)]
+        E, a, K, Pg, Py, Pt, Pr, _, _ = split_column_projectors(A, env, y, chi, record, order)
+        stage = bra_stage_alt if order == "alternative" else bra_stage
+        new = [stage(E[x], a[x], K[x], Pt[(x - 1) % Lx], Pr[x], Pt[x]) for x in range(Lx)]
         yn = (y + 1) % Ly
         for x in range(Lx):
             d = dict(env[x][yn])
@@ -567,25 +700,26 @@ def split_left_move(A, env, chi, record=None):
     return env
 
 
-def split_move(A, env, direction: int, chi: int):
+def split_move(A, env, direction: int, chi: int, order: str = "standard"):
     """Directional move (0 left, 1 top, 2 right, 3 bottom) of the split CTMRG."""
-    return in_frame(direction, lambda a, e: split_left_move(a, e, chi), A, env, split=True)
+    return in_frame(direction, lambda a, e: split_left_move(a, e, chi, order=order), A, env, split=True)
 
 
-def split_sweep(A, env, chi):
+def split_sweep(A, env, chi, order: str = "standard"):
     """One full step: left, top, right, bottom moves in sequence."""
     for d in range(4):
-        env = split_move(A, env, d, chi)
+        env = split_move(A, env, d, chi, order)
     return env
 
 
-def split_ctmrg(A, chi: int, sweeps: int, env=None):
-    """Initial environment (if not given) followed by ``sweeps`` full steps."""
+def split_ctmrg(A, chi: int, sweeps: int, env=None, order: str = "standard"):
+    """Initial environment (if not given) followed by ``sweeps`` full steps.
+    order: "standard" or "alternative" yellow/red order (App. B)."""
     A = A if isinstance(A, list) else as_cell(A)
     if env is None:
         env = initial_env(A, chi, split=True)
     for _ in range(sweeps):
-        env = split_sweep(A, env, chi)
+        env = split_sweep(A, env, chi, order)
     return env
 
 

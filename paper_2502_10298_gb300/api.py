@@ -10,7 +10,7 @@ import torch
 __all__ = [
     "load_library", "Config", "sctm_create", "sctm_destroy", "split_ctmrg_init", "split_ctmrg_move",
     "split_ctmrg_sweeps", "split_ctmrg_run", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
-    "sctm_get_env", "sctm_workspace_high_water", "sctm_profile", "sctm_svd", "sctm_svd_noalloc", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
+    "sctm_get_env", "sctm_workspace_high_water", "sctm_set_limits", "sctm_profile", "sctm_svd", "sctm_svd_noalloc", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
                 ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("power_steps", ctypes.c_int), ("randomized_min", ctypes.c_int),
                 ("adjoint_cg_steps", ctypes.c_int), ("adjoint_band", ctypes.c_int),
-                ("rank_extra", ctypes.c_int), ("algorithm", ctypes.c_int)]
+                ("rank_extra", ctypes.c_int), ("algorithm", ctypes.c_int), ("projector_order", ctypes.c_int)]
 
 
 _lib = None
@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "sctm_svd": (i, [vp, i, i, vp, vp, vp, vp]),
         "sctm_einsum": (i, [vp, ctypes.c_char_p, vp, _ip, vp, _ip, vp, _ip, d, d]),
         "sctm_svd_noalloc": (i, [i, i, vp, vp, vp, vp, vp]),
+        "sctm_set_limits": (i, [vp, i, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -92,10 +93,10 @@ def _hp(a):
 
 def sctm_create(Lx, Ly, p, D, chi, precision=0, svd_cutoff=0.0, lorentz_eps=0.0, workspace_bytes=0,
                 stream=None, power_steps=0, randomized_min=0, adjoint_cg_steps=0, adjoint_band=0, algorithm=0,
-                rank_extra=0):
+                rank_extra=0, projector_order=0):
     lib = load_library()
     cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes, power_steps,
-                 randomized_min, adjoint_cg_steps, adjoint_band, rank_extra, algorithm)
+                 randomized_min, adjoint_cg_steps, adjoint_band, rank_extra, algorithm, projector_order)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     h = ctypes.c_void_p()
@@ -252,6 +253,12 @@ def sctm_svd_noalloc(M: torch.Tensor, U=None, S=None, V=None):
     return U, S, V
 
 
+def sctm_set_limits(h, svd_max_sweeps: int = 0, pipeline_wait_s: float = -1.0):
+    """Bounded-loop limits of the handle (fault-injection hook): Jacobi sweeps
+    (<= 0: default) and the tensor-core main-loop wait (< 0: default 2 s)."""
+    _check(h, _lib.sctm_set_limits(h, int(svd_max_sweeps), float(pipeline_wait_s)))
+
+
 def sctm_workspace_high_water(h) -> int:
     v = ctypes.c_size_t()
     _check(h, _lib.sctm_workspace_high_water(h, ctypes.byref(v)))
@@ -264,6 +271,7 @@ class SplitCTMRG:
     def __init__(self, Lx, Ly, p, D, chi, **kw):
         self.Lx, self.Ly, self.p, self.D, self.chi = Lx, Ly, p, D, chi
         self.conventional = kw.get("algorithm", 0) == 1
+        self.order = kw.get("projector_order", 0)
         self.h = sctm_create(Lx, Ly, p, D, chi, **kw)
 
     def close(self):
@@ -305,5 +313,7 @@ class SplitCTMRG:
         return energy_grad(self.h, A, sweeps, h_nn, h_diag)
 
     def projectors(self, direction, x, y, colour):
-        alpha = self.chi * self.D * (self.p if colour == 3 else 1)
+        # the colour that carries the physical leg: red (order 0) or yellow (order 1)
+        phys = (colour == 3) if self.order == 0 else (colour == 2)
+        alpha = self.chi * self.D * (self.p if phys else 1)
         return ctmrg_projectors(self.h, direction, x, y, colour, self.chi, alpha)

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsplitctmrg.so")
-SOURCES = ["contract.cu", "jacobi.cu", "misc.cu", "ops.cu", "ctmrg.cu", "capi.cu", "prof.cu", "tc_gemm.cu", "chol.cu", "noalloc.cu"]
+SOURCES = ["contract.cu", "jacobi.cu", "misc.cu", "ops.cu", "ctmrg.cu", "capi.cu", "prof.cu", "tc_gemm.cu", "chol.cu", "noalloc.cu", "tc_slices.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

@@ -130,6 +130,8 @@ void bind_store(sctm_handle h, double* base) {
 // holds the environment of the last call that completed).
 void rollback(sctm_handle h, size_t arena_mark) {
   h->c.arena.release(arena_mark);
+  h->c.arena.release_high(h->c.arena.capacity());   // forward-pass caches of the failed call
+  h->c.decomp = Ctx::DecompCache();
   h->c.tape.active = false;
   h->c.tape.ops.clear();
   if (h->store && h->A) {
@@ -320,12 +322,13 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
   int rc = guard(h.get(), [&]() {
     SCTM_CHECK(cfg->Lx >= 1 && cfg->Ly >= 1 && cfg->p >= 1 && cfg->D >= 1 && cfg->chi >= 1, "bad dimensions");
     SCTM_CHECK(cfg->D * cfg->D <= cfg->chi, "chi must be >= D^2");
-    SCTM_CHECK(cfg->precision >= 0 && cfg->precision <= 3, "precision must be 0 (FP64), 1, 2 (mixed) or 3");
+    SCTM_CHECK(cfg->precision >= 0 && cfg->precision <= 4, "precision must be 0 (FP64), 1, 2, 4 (mixed) or 3");
     Params& P = h->P;
     P.Lx = cfg->Lx, P.Ly = cfg->Ly, P.p = cfg->p, P.D = cfg->D, P.chi = cfg->chi;
     P.mixed = (cfg->precision >= 1);   // randomized projectors for large truncated spaces
-    h->c.fp32_compute = (cfg->precision == 1 || cfg->precision == 2);
-    h->c.tensor_cores = (cfg->precision == 1);
+    h->c.fp32_compute = (cfg->precision == 1 || cfg->precision == 2 || cfg->precision == 4);
+    h->c.tensor_cores = (cfg->precision == 1 || cfg->precision == 4);
+    h->c.bf16_slices = (cfg->precision == 4);
     // FP32-level contractions resolve the singular vectors of values near 1e-6 s_max
     // only to O(0.1); from 1e-5 s_max up they are accurate enough for the gradient
     if (P.mixed) P.cutoff = h->c.fp32_compute ? 1e-5 : 1e-6;
@@ -342,6 +345,8 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     SCTM_CHECK(cfg->adjoint_band >= 0, "adjoint_band must be >= 0");
     P.adjoint_band = cfg->adjoint_band > 0 ? cfg->adjoint_band - 1 : -1;
     if (cfg->lorentz_eps > 0) P.eps_l = cfg->lorentz_eps;
+    SCTM_CHECK(cfg->projector_order == 0 || cfg->projector_order == 1, "projector_order must be 0 or 1");
+    P.order = cfg->projector_order;
     h->c.stream = (cudaStream_t)stream;
     SCTM_CHECK(cfg->algorithm == 0 || cfg->algorithm == 1, "algorithm must be 0 (split) or 1 (conventional)");
     P.conventional = (cfg->algorithm == 1);
@@ -538,8 +543,17 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
     save_env(h, ck);
     bind_store(h, ck);
     size_t top = c.arena.mark();
+    // the randomized decompositions of every move are kept (arena high stack)
+    // for the taped recomputation of that move in the reverse pass
+    std::vector<std::vector<std::array<Tensor, 3>>> decomp(nmoves);
+    std::vector<size_t> high_mark(nmoves);
     for (int mv = 0; mv < nmoves; ++mv) {
+      high_mark[mv] = c.arena.mark_high();
+      c.decomp = Ctx::DecompCache();
+      c.decomp.mode = 1;
       move(c, P, h->cell, mv % 4);
+      decomp[mv] = std::move(c.decomp.entries);
+      c.decomp = Ctx::DecompCache();
       save_env(h, ck + (mv + 1) * nE);
       bind_store(h, ck + (mv + 1) * nE);
       c.arena.release(top);
@@ -558,13 +572,19 @@ int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, const doubl
       bind_leaves(h, ck + mv * nE);
       std::vector<SiteEnv> leaves = h->cell.env;
       const size_t tm = c.tape.mark();
+      c.decomp = Ctx::DecompCache();
+      c.decomp.mode = 2;
+      c.decomp.entries = std::move(decomp[mv]);
       move(c, P, h->cell, mv % 4);
+      SCTM_CHECK(c.decomp.next == c.decomp.entries.size(), "decomposition cache: entries left over");
+      c.decomp = Ctx::DecompCache();
       seed_env_grad(h, gbuf);
       c.tape.backward_from(tm);
       h->cell.env = leaves;
       read_env_grad(h, gbuf);
       c.tape.active = false;
       c.arena.release(top);
+      c.arena.release_high(high_mark[mv]);
     }
     // reverse through the initial environment (recorded in the forward)
     h->cell.env = init_out;
@@ -625,7 +645,8 @@ int sctm_svd(sctm_handle h, int m, int n, const double* M_dev, double* U_dev, do
     double* work = nullptr;
     size_t wn = svd_work_doubles(m, n, 1);
     if (wn) work = h->c.arena.alloc((long long)wn);
-    launch_svd(m, n, 1, M_dev, U_dev, S_dev, V_dev, work, h->c.svd_status, h->c.stream);
+    launch_svd(m, n, 1, M_dev, U_dev, S_dev, V_dev, work, h->c.svd_status, h->c.stream, 0.0, 0.0,
+               h->c.svd_max_sweeps);
     check_svd(h);
     h->c.arena.release(mk);
   });
@@ -678,6 +699,14 @@ int sctm_profile(sctm_handle h, int enable, double* out) {
 
 int sctm_workspace_high_water(sctm_handle h, size_t* bytes) {
   return guard(h, [&]() { *bytes = h->c.arena.high_water(); });
+}
+
+int sctm_set_limits(sctm_handle h, int svd_max_sweeps, double pipeline_wait_s) {
+  return guard(h, [&]() {
+    SCTM_CHECK(pipeline_wait_s <= 60.0, "pipeline_wait_s must be at most 60 s");
+    h->c.svd_max_sweeps = svd_max_sweeps > 0 ? svd_max_sweeps : 60;
+    h->c.pipe_wait_ns = pipeline_wait_s < 0 ? 2000000000ull : (unsigned long long)(pipeline_wait_s * 1e9);
+  });
 }
 
 }  // extern "C"

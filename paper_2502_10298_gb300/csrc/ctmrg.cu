@@ -35,7 +35,8 @@ static std::vector<SVDResult> svd_batch(Ctx& c, const std::vector<Tensor>& Ms) {
   // discarded afterwards, so their (noise-level) columns need not converge
   // the factors come from mixed-precision products (rounding about 1e-7), so
   // orthogonality to 1e-11 is ample
-  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 2.0e-29, 1e-11);
+  launch_svd(n, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 2.0e-29, 1e-11,
+             c.svd_max_sweeps);
   for (int i = 0; i < nb; ++i) out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};
   return out;
 }
@@ -50,6 +51,18 @@ struct Fp64Scope {
     on = false;
   }
   ~Fp64Scope() { end(); }
+};
+
+// In the BF16-slice mode (precision 4), contractions of this scope whose shape
+// fits the tensor-core tiles take the slice kernel whatever their size, and the
+// others run in FP64 on the CUDA cores: the randomized projectors resolve the
+// small singular directions from products with rho, and their reverse pass
+// divides by those singular values, so FP32-level rounding there would swamp
+// the gradient.  No effect in the other precisions.
+struct AccurateScope {
+  Ctx& c;
+  explicit AccurateScope(Ctx& cx) : c(cx) { ++c.accurate; }
+  ~AccurateScope() { --c.accurate; }
 };
 
 // G = Y^T Y in FP64.
@@ -90,6 +103,7 @@ struct Trunc {
 };
 static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB,
                                                int r, int power_steps) {
+  AccurateScope acc(c);
   const size_t nb = rT.size();
   std::vector<Tensor> Y(nb);
   for (size_t i = 0; i < nb; ++i) {
@@ -158,6 +172,7 @@ static constexpr double kComplementMinRel = 1e-3;
 
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l, int cg_steps) {
+  AccurateScope acc(c);
   // FP64 arithmetic up to M_bar's factors: the complement terms divide
   // P U_bar by s_i, and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level
   // rounding of it, amplified by 1/s_i up to the inverse cutoff, swamps the
@@ -272,6 +287,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
 // randomized subspace iteration (randomized_svd_batch) and the reverse pass uses
 // the truncated-SVD adjoint above.
 static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, const Trunc& t) {
+  AccurateScope acc(c);
   const int k = P.chi;
   bool tap = c.tape.active;
   {
@@ -329,10 +345,39 @@ std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tens
     }
   }
   if (!ri.empty()) {
-    bool tap = c.tape.active;
-    c.tape.active = false;
-    std::vector<Trunc> t = randomized_svd_batch(c, bT, bB, P.chi + P.rank_extra, P.power_steps);
-    c.tape.active = tap;
+    const int r = P.chi + P.rank_extra;
+    std::vector<Trunc> t(ri.size());
+    Ctx::DecompCache& dc = c.decomp;
+    if (dc.mode == 2) {
+      // replay the forward pass's decompositions of this move, in call order
+      SCTM_CHECK(dc.next + ri.size() <= dc.entries.size(), "decomposition cache: fewer entries than calls");
+      for (size_t j = 0; j < ri.size(); ++j) {
+        const std::array<Tensor, 3>& e = dc.entries[dc.next++];
+        SCTM_CHECK(e[0].shape[0] == bB[j].shape[0] && e[0].shape[1] == r, "decomposition cache: shape mismatch");
+        t[j] = Trunc{e[0], e[1], e[2]};
+      }
+    } else {
+      bool tap = c.tape.active;
+      c.tape.active = false;
+      t = randomized_svd_batch(c, bT, bB, r, P.power_steps);
+      if (dc.mode == 1) {
+        for (size_t j = 0; j < ri.size(); ++j) {
+          std::array<Tensor, 3> e;
+          const Tensor* src[3] = {&t[j].U, &t[j].S, &t[j].V};
+          for (int q = 0; q < 3; ++q) {
+            Tensor d = *src[q];
+            d.grad = nullptr;
+            d.data = c.arena.alloc_high(src[q]->numel());
+            long long st = 1;
+            for (int i = d.nd - 1; i >= 0; --i) d.stride[i] = st, st *= d.shape[i];
+            copy_into(c, *src[q], d);
+            e[q] = d;
+          }
+          dc.entries.push_back(e);
+        }
+      }
+      c.tape.active = tap;
+    }
     for (size_t j = 0; j < ri.size(); ++j) out[ri[j]] = finish_randomized(c, P, bT[j], bB[j], t[j]);
   }
   return out;
@@ -471,14 +516,26 @@ static Tensor yellow_rhoT(Ctx& c, SiteEnv& E, const Tensor& A) {
 }
 
 // Fig. 8 lower box.  Rows (A'.s, A'.u', T2b.j), cols (T4b.q, T3k.d).
-static Tensor yellow_rhoB(Ctx& c, SiteEnv& E, const Tensor& A) {
+static Tensor yellow_lower(Ctx& c, SiteEnv& E, const Tensor& A) {   // [d, v, q, j, z, e]
   Tensor Y = einsum(c, "mn,kdm->nkd", E[C4], E[T3k]);
   Y = einsum(c, "nkd,nvq->kdvq", Y, E[T4b]);
   Tensor Z = einsum(c, "gh,hek->gek", E[C3], E[T3b]);
   Z = einsum(c, "jzg,gek->jzek", E[T2b], Z);
-  Y = einsum(c, "kdvq,jzek->dvqjze", Y, Z);
-  Y = einsum(c, "dvqjze,swvez->swjqd", Y, A);
-  return mat(Y, 3);
+  return einsum(c, "kdvq,jzek->dvqjze", Y, Z);
+}
+static Tensor yellow_rhoB(Ctx& c, SiteEnv& E, const Tensor& A) {
+  return mat(einsum(c, "dvqjze,swvez->swjqd", yellow_lower(c, E, A), A), 3);
+}
+
+// Alternative order (App. B): the same networks with the ket's physical leg on
+// the truncated side.  Rows (T4k.q, A.d, A.s), cols (T1b.u', T2k.j); and rows
+// (A'.u', T2b.j), cols (T4b.q, T3k.d, A'.s).
+static Tensor yellow_alt_rhoT(Ctx& c, SiteEnv& E, const Tensor& A) {
+  Tensor X = upper_ket_row(c, E, A);
+  return mat(einsum(c, "qskrwf,frj->qkswj", X, E[T2k]), 3);
+}
+static Tensor yellow_alt_rhoB(Ctx& c, SiteEnv& E, const Tensor& A) {
+  return mat(einsum(c, "dvqjze,swvez->wjqds", yellow_lower(c, E, A), A), 2);
 }
 
 // Eqs. (splitCTMRG_*), ket layer: absorb A and apply green (E-cut) and yellow
@@ -490,9 +547,16 @@ static KetStage ket_stage(Ctx& c, SiteEnv& E, const Tensor& A, const ProjPair& g
   K.C1k = einsum(c, "bui,gbu->ig", X, ga.up);
   Tensor Z = einsum(c, "bug,qlb->ugql", ga.dn, E[T4k]);
   Z = einsum(c, "ugql,suldr->gqsdr", Z, A);
-  K.T4kk = einsum(c, "gqsdr,yqd->grys", Z, y.up);
-  Z = einsum(c, "qky,nvq->kynv", y.dn, E[T4b]);
-  K.T4bk = einsum(c, "kynv,tnk->yvt", Z, gb.up);
+  if (y.up.nd == 4) {
+    // alternative order: yellow acts on (q, d, s); the physical leg moves to T4b_k
+    K.T4kk = einsum(c, "gqsdr,yqds->gry", Z, y.up);
+    Z = einsum(c, "qksy,nvq->ksynv", y.dn, E[T4b]);
+    K.T4bk = einsum(c, "ksynv,tnk->yvts", Z, gb.up);
+  } else {
+    K.T4kk = einsum(c, "gqsdr,yqd->grys", Z, y.up);
+    Z = einsum(c, "qky,nvq->kynv", y.dn, E[T4b]);
+    K.T4bk = einsum(c, "kynv,tnk->yvt", Z, gb.up);
+  }
   Z = einsum(c, "mn,kdm->nkd", E[C4], E[T3k]);
   K.C4k = einsum(c, "nkd,ndt->tk", Z, gb.dn);
   return K;
@@ -500,6 +564,12 @@ static KetStage ket_stage(Ctx& c, SiteEnv& E, const Tensor& A, const ProjPair& g
 
 // column y of the upper 2x2 half after the ket stage: [r, c, t, e, z]
 static Tensor upper_left_k(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K) {
+  if (K.alt()) {
+    Tensor X = einsum(c, "ig,gry->iry", K.C1k, K.T4kk);
+    X = einsum(c, "iry,iwc->rywc", X, E[T1b]);
+    X = einsum(c, "rywc,yvts->rwcvts", X, K.T4bk);
+    return einsum(c, "rwcvts,swvez->rctez", X, A);
+  }
   Tensor X = einsum(c, "ig,grys->irys", K.C1k, K.T4kk);
   X = einsum(c, "irys,iwc->ryswc", X, E[T1b]);
   X = einsum(c, "ryswc,yvt->rswcvt", X, K.T4bk);
@@ -519,6 +589,11 @@ static Tensor upper_right(Ctx& c, SiteEnv& E, const Tensor& A) {
 // column y of the lower half after the ket stage: [h, w, z, g, r]
 static Tensor lower_left_k(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K) {
   Tensor Z = einsum(c, "tk,hek->the", K.C4k, E[T3b]);
+  if (K.alt()) {
+    Z = einsum(c, "the,yvts->heyvs", Z, K.T4bk);
+    Z = einsum(c, "heyvs,swvez->hywz", Z, A);
+    return einsum(c, "hywz,gry->hwzgr", Z, K.T4kk);
+  }
   Z = einsum(c, "the,yvt->heyv", Z, K.T4bk);
   Z = einsum(c, "heyv,swvez->hyswz", Z, A);
   return einsum(c, "hyswz,grys->hwzgr", Z, K.T4kk);
@@ -567,6 +642,30 @@ static Tensor red_rhoB(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K, S
   return mat(einsum(c, "jDhSWv,hyswv->DSWjysw", W, Z), 4);
 }
 
+// red of the alternative order: rows (T4k_k.y, T1b.u'), cols (A.d, A.s, T1b.u', T2k.j of y+1)
+static Tensor red_alt_rhoT(Ctx& c, SiteEnv& E, const KetStage& K, SiteEnv& E2, const Tensor& A2) {
+  Tensor X = einsum(c, "ig,gry->iry", K.C1k, K.T4kk);
+  X = einsum(c, "iry,iwc->rywc", X, E[T1b]);
+  Tensor Y = einsum(c, "cui,iWC->cuWC", E2[T1k], E2[T1b]);
+  Y = einsum(c, "cuWC,Cf->cuWf", Y, E2[C2]);
+  Y = einsum(c, "cuWf,fRj->cuWRj", Y, E2[T2k]);
+  Y = einsum(c, "cuWRj,SulDR->cWjSlD", Y, A2);
+  return mat(einsum(c, "rywc,cWjSrD->ywDSWj", X, Y), 2);
+}
+
+// rows (T3k.d, A'.s, A'.u', T2b.j of y+1), cols (T4b_k.y, A'.u'); the bra closes T4b_k's physical leg
+static Tensor red_alt_rhoB(Ctx& c, SiteEnv& E, const Tensor& A, const KetStage& K, SiteEnv& E2,
+                           const Tensor& A2) {
+  Tensor Z = einsum(c, "tk,hek->the", K.C4k, E[T3b]);
+  Z = einsum(c, "the,yvts->heyvs", Z, K.T4bk);
+  Z = einsum(c, "heyvs,swvez->hywz", Z, A);
+  Tensor W = einsum(c, "jZG,GH->jZH", E2[T2b], E2[C3]);
+  W = einsum(c, "jZH,HEK->jZEK", W, E2[T3b]);
+  W = einsum(c, "jZEK,KDh->jZEDh", W, E2[T3k]);
+  W = einsum(c, "jZEDh,SWvEZ->jDhSWv", W, A2);
+  return mat(einsum(c, "jDhSWv,hywv->DSWjyw", W, Z), 4);
+}
+
 static ProjPair shaped(const ProjPair& p, int a0, int a1, int a2 = 0) {
   ProjPair q = p;
   int k = p.up.shape[0];
@@ -591,14 +690,15 @@ void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& o
     rT.push_back(green_rhoT(c, cell.e(x, y), cell.a(x, y)));
     rB.push_back(green_rhoB(c, cell.e(x + 1, y), cell.a(x + 1, y)));
   }
+  const bool alt = P.order == 1;
   for (int x = 0; x < Lx; ++x) {
-    rT.push_back(yellow_rhoT(c, cell.e(x, y), cell.a(x, y)));
-    rB.push_back(yellow_rhoB(c, cell.e(x, y), cell.a(x, y)));
+    rT.push_back(alt ? yellow_alt_rhoT(c, cell.e(x, y), cell.a(x, y)) : yellow_rhoT(c, cell.e(x, y), cell.a(x, y)));
+    rB.push_back(alt ? yellow_alt_rhoB(c, cell.e(x, y), cell.a(x, y)) : yellow_rhoB(c, cell.e(x, y), cell.a(x, y)));
   }
   std::vector<ProjPair> pk = projectors(c, P, rT, rB);
   for (int x = 0; x < Lx; ++x) {
     out.g[x] = shaped(pk[x], chi, D);
-    out.y[x] = shaped(pk[Lx + x], chi, D);
+    out.y[x] = alt ? shaped(pk[Lx + x], chi, D, p) : shaped(pk[Lx + x], chi, D);
   }
   for (int x = 0; x < Lx; ++x)
     out.K[x] = ket_stage(c, cell.e(x, y), cell.a(x, y), out.g[(x + Lx - 1) % Lx], out.y[x], out.g[x]);
@@ -611,13 +711,18 @@ void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& o
     rB.push_back(teal_rhoB(c, cell.e(xp, y), cell.a(xp, y), out.K[xp], cell.e(xp, y + 1), cell.a(xp, y + 1)));
   }
   for (int x = 0; x < Lx; ++x) {
-    rT.push_back(red_rhoT(c, cell.e(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
-    rB.push_back(red_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+    if (alt) {
+      rT.push_back(red_alt_rhoT(c, cell.e(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+      rB.push_back(red_alt_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+    } else {
+      rT.push_back(red_rhoT(c, cell.e(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+      rB.push_back(red_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
+    }
   }
   std::vector<ProjPair> pb = projectors(c, P, rT, rB);
   for (int x = 0; x < Lx; ++x) {
     out.t[x] = shaped(pb[x], chi, D);
-    out.r[x] = shaped(pb[Lx + x], chi, p, D);
+    out.r[x] = alt ? shaped(pb[Lx + x], chi, D) : shaped(pb[Lx + x], chi, p, D);
   }
 }
 
@@ -638,10 +743,19 @@ void left_move(Ctx& c, const Params& P, Cell& cell) {
       const ProjPair& tb = t[x];
       Tensor X = einsum(c, "ig,iwc->gwc", K[x].C1k, E[T1b]);
       Tensor nC1 = einsum(c, "gwc,Tgw->cT", X, ta.up);
-      Tensor Z = einsum(c, "gwT,grys->Twrys", ta.dn, K[x].T4kk);
-      Tensor nT4k = einsum(c, "Twrys,Pysw->PrT", Z, r[x].up);
-      Z = einsum(c, "yswP,yvt->swPvt", r[x].dn, K[x].T4bk);
-      Z = einsum(c, "swPvt,swvez->Ptez", Z, A);
+      Tensor Z, nT4k;
+      if (K[x].alt()) {
+        // alternative order: red acts on (y, u'); the bra closes T4b_k's physical leg
+        Z = einsum(c, "gwT,gry->Twry", ta.dn, K[x].T4kk);
+        nT4k = einsum(c, "Twry,Pyw->PrT", Z, r[x].up);
+        Z = einsum(c, "ywP,yvts->wPvts", r[x].dn, K[x].T4bk);
+        Z = einsum(c, "wPvts,swvez->Ptez", Z, A);
+      } else {
+        Z = einsum(c, "gwT,grys->Twrys", ta.dn, K[x].T4kk);
+        nT4k = einsum(c, "Twrys,Pysw->PrT", Z, r[x].up);
+        Z = einsum(c, "yswP,yvt->swPvt", r[x].dn, K[x].T4bk);
+        Z = einsum(c, "swPvt,swvez->Ptez", Z, A);
+      }
       Tensor nT4b = einsum(c, "Ptez,Ote->OzP", Z, tb.up);
       Z = einsum(c, "tk,hek->the", K[x].C4k, E[T3b]);
       Tensor nC4 = einsum(c, "the,teO->hO", Z, tb.dn);

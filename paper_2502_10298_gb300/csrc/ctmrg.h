@@ -37,6 +37,7 @@ struct Params {
   int adjoint_cg_steps = 0;   // randomized projectors' adjoint: CG steps for the complement coupling
   int adjoint_band = -1;      // randomized projectors' adjoint: computed triplets beyond chi coupled exactly (-1: all)
   int randomized_min = 256;   // randomized projectors only when the truncated space has >= this dimension
+  int order = 0;              // 0: the physical leg truncated by red (Sec. II.B); 1: by yellow (App. B)
 };
 
 struct ProjPair {
@@ -48,7 +49,10 @@ struct ProjPair {
 ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB);
 
 struct KetStage {
-  Tensor C1k, T4kk, T4bk, C4k;   // C1k[i,g] T4kk[g,r,y,s] T4bk[y,v,t] C4k[t,k]
+  // C1k[i,g] T4kk[g,r,y,s] T4bk[y,v,t] C4k[t,k]; in the alternative order
+  // (physical leg truncated by yellow) T4kk[g,r,y] and T4bk[y,v,t,s]
+  Tensor C1k, T4kk, T4bk, C4k;
+  bool alt() const { return T4kk.nd == 3; }
 };
 
 // All projectors of one column of a left move (green, yellow, teal, red per

@@ -314,14 +314,14 @@ constexpr int kMaxDevices = 64;
 static bool fits_smem(int m, int n) { return (long long)(m + n) * n * 8 <= 40 * 1024; }
 
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V, double* work,
-                int* status, cudaStream_t s, double noise_rel, double tol_rel) {
+                int* status, cudaStream_t s, double noise_rel, double tol_rel, int max_sweeps) {
   if (batch == 0 || n == 0) return;
   SCTM_CHECK(m >= n, "svd expects rows >= columns");
   char tag[96] = {0};
   if (prof_enabled())
     std::snprintf(tag, sizeof(tag), "jacobi m%d n%d batch%d%s", m, n, batch, fits_smem(m, n) ? " smem" : " coop");
   ProfTag profile_label(prof_enabled() ? tag : nullptr);
-  const int max_sweeps = 60;
+  SCTM_CHECK(max_sweeps >= 1, "svd: max_sweeps must be >= 1");
   const double tol = tol_rel > 0.0 ? tol_rel : 2.3e-16 * 4.0 * sqrt((double)m);
   const int in_smem = fits_smem(m, n);
   size_t smem = in_smem ? (size_t)(m + n) * n * sizeof(double) : 0;

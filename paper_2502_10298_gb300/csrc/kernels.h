@@ -21,9 +21,23 @@ void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, con
 // scratch: tc_scratch_floats(d) floats, 128-byte aligned; status: device word
 // set to -2 if a pipeline wait timed out.
 bool tc_eligible(const ContractDesc& d);
+// the shape conditions of tc_eligible alone (tiles representable, M, N >= 64,
+// K >= 128), without its minimum amount of work
+bool tc_shape_ok(const ContractDesc& d);
 size_t tc_scratch_floats(const ContractDesc& d);
+// wait_ns: main-loop mbarrier wait limit (global time); the drain waits after a
+// timeout keep the full default limit of two seconds
 void launch_contract_tc(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
-                        float* scratch, int* status);
+                        float* scratch, int* status, unsigned long long wait_ns = 2000000000ull);
+
+// Tensor-core form with FP64-grade accuracy (precision 4): operands scaled per
+// row / column by powers of two and split into four BF16 digit slices, ten
+// tcgen05 kind::f16 products per 16 of K with exact FP32 accumulation of the
+// two leading levels, FP64 output (tc_slices.cu).  Same eligibility as the
+// 3xTF32 form.  scratch: slice_scratch_bytes(d) bytes; status as above.
+size_t slice_scratch_bytes(const ContractDesc& d);
+void launch_contract_slices(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
+                            void* scratch, int* status, unsigned long long wait_ns = 2000000000ull);
 
 // deterministic N(0,1) test matrix (counter-based hash + Box-Muller), rows x cols
 void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s);
@@ -35,8 +49,10 @@ void launch_gaussian(long long rows, long long cols, unsigned long long seed, do
 // decompositions whose noise-level directions are discarded afterwards).
 // tol_rel > 0 replaces the default orthogonality threshold |w_i.w_j| <= tol |w_i||w_j|
 // (4 eps sqrt(m)) for decompositions that need less.
+// max_sweeps bounds the Jacobi sweeps (a run that reaches it sets status word 0 to -1).
 void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, double* V,
-                double* work, int* status, cudaStream_t s, double noise_rel = 0.0, double tol_rel = 0.0);
+                double* work, int* status, cudaStream_t s, double noise_rel = 0.0, double tol_rel = 0.0,
+                int max_sweeps = 60);
 size_t svd_work_doubles(int m, int n, int batch);
 
 // out[g] = alpha * in[g] + beta * out[g] over one index group g (strides sa = in, sc = out).

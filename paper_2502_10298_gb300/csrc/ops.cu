@@ -18,19 +18,30 @@ void Arena::reserve(size_t bytes) {
   if (base_) cudaFree(base_);
   base_ = nullptr;
   SCTM_CUDA(cudaMalloc(&base_, bytes));
-  cap_ = bytes;
+  cap_ = bytes & ~(size_t)255;
   top_ = 0;
+  hi_ = cap_;
 }
 
 double* Arena::alloc(long long n) {
   size_t bytes = ((size_t)std::max<long long>(n, 1) * sizeof(double) + 255) & ~(size_t)255;
-  if (top_ + bytes > cap_)
-    throw ArgError("device workspace exhausted (" + std::to_string((top_ + bytes) >> 20) + " MiB needed, " +
-                   std::to_string(cap_ >> 20) + " MiB reserved)");
+  if (top_ + bytes > hi_)
+    throw ArgError("device workspace exhausted (" + std::to_string((top_ + bytes + cap_ - hi_) >> 20) +
+                   " MiB needed, " + std::to_string(cap_ >> 20) + " MiB reserved)");
   double* p = reinterpret_cast<double*>(base_ + top_);
   top_ += bytes;
-  high_ = std::max(high_, top_);
+  high_ = std::max(high_, top_ + (cap_ - hi_));
   return p;
+}
+
+double* Arena::alloc_high(long long n) {
+  size_t bytes = ((size_t)std::max<long long>(n, 1) * sizeof(double) + 255) & ~(size_t)255;
+  if (hi_ < top_ + bytes)
+    throw ArgError("device workspace exhausted (" + std::to_string((top_ + bytes + cap_ - hi_) >> 20) +
+                   " MiB needed, " + std::to_string(cap_ >> 20) + " MiB reserved)");
+  hi_ -= bytes;
+  high_ = std::max(high_, top_ + (cap_ - hi_));
+  return reinterpret_cast<double*>(base_ + hi_);
 }
 
 Tensor Tensor::reshape(std::initializer_list<int> s) const {
@@ -187,16 +198,24 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
                   c.fp32_compute ? "" : " f64");
     prof_set_tag(tag);
   }
-  if (c.fp32_compute && c.tensor_cores && tc_eligible(d)) {
+  // inside an accurate scope of the BF16-slice mode, every contraction whose
+  // shape fits the tiles takes the slice kernel and the rest run in FP64
+  const bool accurate = c.bf16_slices && c.accurate > 0 && c.fp32_compute;
+  if (c.fp32_compute && c.tensor_cores && (accurate ? tc_shape_ok(d) : tc_eligible(d))) {
     size_t mk = c.arena.mark();
-    float* scratch = reinterpret_cast<float*>(c.arena.alloc((long long)(tc_scratch_floats(d) + 1) / 2));
-    launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32);
+    if (c.bf16_slices) {
+      void* scratch = c.arena.alloc((long long)(slice_scratch_bytes(d) + 7) / 8);
+      launch_contract_slices(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns);
+    } else {
+      float* scratch = reinterpret_cast<float*>(c.arena.alloc((long long)(tc_scratch_floats(d) + 1) / 2));
+      launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns);
+    }
     c.arena.release(mk);   // stream-ordered: later work on the stream reuses it after the GEMM
   } else {
     const size_t wn = contract_scratch_doubles(d);
     size_t mk = c.arena.mark();
     double* scratch = wn ? c.arena.alloc((long long)wn) : nullptr;
-    launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute, scratch);
+    launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute && !accurate, scratch);
     c.arena.release(mk);
   }
   if (prof_enabled()) prof_set_tag("");
@@ -306,7 +325,7 @@ std::vector<SVDResult> svd_many(Ctx& c, const std::vector<Tensor>& Ms, double ep
   double* work = nullptr;
   size_t wn = svd_work_doubles(m, n, nb);
   if (wn) work = c.arena.alloc((long long)wn);
-  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream);
+  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 0.0, 0.0, c.svd_max_sweeps);
   if (!tap) c.arena.release(mk);  // later work is stream-ordered after the kernel
   for (int i = 0; i < nb; ++i) {
     out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};

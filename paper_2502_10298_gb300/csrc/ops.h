@@ -2,6 +2,7 @@
 // the kernels of this directory and, while the tape is active, records the
 // closure that accumulates the adjoints of its inputs.
 #pragma once
+#include <array>
 #include <string>
 #include <vector>
 
@@ -20,6 +21,19 @@ struct Ctx {
   bool svd_failed = false;
   bool fp32_compute = false;     // mixed mode: contractions in FP32 arithmetic
   bool tensor_cores = true;      // mixed mode: large contractions on tcgen05 (3xTF32)
+  bool bf16_slices = false;      // tensor-core contractions as BF16 digit slices (precision 4)
+  int accurate = 0;              // > 0: inside an AccurateScope (see ctmrg.cu)
+  // Randomized projector decompositions (U, S, V of each truncated SVD) of one
+  // move: recorded by the forward pass into the arena's high stack and replayed
+  // by the taped recomputation of the same move in the reverse pass, which
+  // then skips the subspace iteration.  mode 0 off, 1 record, 2 replay.
+  struct DecompCache {
+    int mode = 0;
+    std::vector<std::array<Tensor, 3>> entries;
+    size_t next = 0;
+  } decomp;
+  int svd_max_sweeps = 60;       // Jacobi sweep limit (fault-injection hook: sctm_set_limits)
+  unsigned long long pipe_wait_ns = 2000000000ull;   // tensor-core main-loop wait limit (same hook)
 
   // new contiguous tensor of the given shape; gradient buffer (zeroed) when taping
   Tensor empty(std::initializer_list<int> shape);

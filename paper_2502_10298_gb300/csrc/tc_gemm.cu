@@ -28,8 +28,11 @@
 #include "common.h"
 #include "kernels.h"
 #include "prof.h"
+#include "tcgen05_util.cuh"
 
 namespace sctm {
+
+using namespace tcx;
 
 namespace {
 
@@ -39,57 +42,6 @@ constexpr int TC_TILE_A = TC_BM * TC_BK * 4;          // bytes of one A slab (16
 constexpr int TC_TILE_B = TC_BN * TC_BK * 4;          // bytes of one B slab (16 KB)
 constexpr int TC_STAGE = 2 * TC_TILE_A + 2 * TC_TILE_B;
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE + 1024;  // + alignment slack (swizzle atoms need 1024 B)
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// wait for the phase of parity `parity`; false on timeout or when another
-// thread of the CTA has already given up (abort flag)
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  const unsigned long long t0 = global_ns();
-  while (!mbar_test(bar, parity)) {
-    if (*abort_flag) return false;
-    if (global_ns() - t0 > TC_WAIT_NS) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-      "[%2];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-
 // shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row atoms 1024 bytes apart
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
@@ -114,11 +66,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
       : "memory");
 }
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-               : "memory");
-}
-
 // Panel of one operand: rows x k gathered from strided FP64, split into TF32 hi/lo.
 struct PackDesc {
   Group bat, rows, k;          // strides of the operand in .sa
@@ -185,19 +132,10 @@ constexpr int TC_CHUNK = 2;   // K slabs accumulated in tensor memory between dr
 constexpr int TC_THREADS_V2 = 64 + 32 * TC_DRAIN_WARPS;
 constexpr int TC_TMEM_COLS = 512;
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-#define SCTM_TMEM_LD8(taddr, v)                                                                   \
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"            \
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]) \
-               : "r"(taddr))
-
 __global__ void __launch_bounds__(TC_THREADS_V2, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcEpi e,
                    int nk_total, int slabs_per_split, double* __restrict__ C, double* __restrict__ W,
-                   long long Wm, long long Wn, int* status) {
+                   long long Wm, long long Wn, int* status, unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -259,7 +197,7 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
       // producer: TMA slabs into the ring
       for (int s = 0; s < nk && !*ab; ++s) {
         const int st = s % TC_STAGES;
-        if (s >= TC_STAGES && !mbar_wait(&empty[st], ((s / TC_STAGES) - 1) & 1, ab)) break;
+        if (s >= TC_STAGES && !mbar_wait(&empty[st], ((s / TC_STAGES) - 1) & 1, ab, wait_ns)) break;
         uint8_t* sp = base + st * TC_STAGE;
         mbar_expect_tx(&full[st], TC_STAGE);
         issued_parity[st] = (s / TC_STAGES) & 1;
@@ -277,8 +215,8 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
         const int st = s % TC_STAGES, ch = s / TC_CHUNK, buf = ch & 1;
         const bool first = (s % TC_CHUNK) == 0;
         const bool last = (s % TC_CHUNK) == TC_CHUNK - 1 || s == nk - 1;
-        if (!mbar_wait(&full[st], (s / TC_STAGES) & 1, ab)) break;
-        if (first && ch >= 2 && !mbar_wait(&acc_empty[buf], ((ch >> 1) - 1) & 1, ab)) break;
+        if (!mbar_wait(&full[st], (s / TC_STAGES) & 1, ab, wait_ns)) break;
+        if (first && ch >= 2 && !mbar_wait(&acc_empty[buf], ((ch >> 1) - 1) & 1, ab, wait_ns)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dmain = tmem + (uint32_t)(buf * 256), dcorr = dmain + 128;
         const uint32_t sa = smem_addr(base + st * TC_STAGE);
@@ -298,7 +236,7 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
       // tracks every MMA issued (normal end or abort); waited before tensor memory is freed
       mma_commit(&done_bar);
       const unsigned long long t0 = global_ns();
-      while (!mbar_test(&done_bar, 0) && global_ns() - t0 < TC_WAIT_NS) {
+      while (!mbar_test(&done_bar, 0) && global_ns() - t0 < kWaitNs) {
       }
     }
     __syncwarp();
@@ -313,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
     const int nch = (nk + TC_CHUNK - 1) / TC_CHUNK;
     for (int ch = 0; ch < nch; ++ch) {
       const int buf = ch & 1;
-      if (!mbar_wait(&acc_full[buf], (ch >> 1) & 1, ab)) {
+      if (!mbar_wait(&acc_full[buf], (ch >> 1) & 1, ab, wait_ns)) {
         ok = false;
         break;
       }
@@ -368,11 +306,11 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
       for (int st = 0; st < TC_STAGES; ++st) {
         if (issued_parity[st] < 0) continue;
         const unsigned long long t0 = global_ns();
-        while (!mbar_test(&full[st], (uint32_t)issued_parity[st]) && global_ns() - t0 < TC_WAIT_NS) {
+        while (!mbar_test(&full[st], (uint32_t)issued_parity[st]) && global_ns() - t0 < kWaitNs) {
         }
       }
       const unsigned long long t0 = global_ns();
-      while (!mbar_test(&done_bar, 0) && global_ns() - t0 < TC_WAIT_NS) {
+      while (!mbar_test(&done_bar, 0) && global_ns() - t0 < kWaitNs) {
       }
     }
     __syncthreads();
@@ -381,22 +319,6 @@ __global__ void __launch_bounds__(TC_THREADS_V2, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    SCTM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-    SCTM_CHECK(q == cudaDriverEntryPointSuccess && p, "cuTensorMapEncodeTiled unavailable");
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
 }
 
 // tensor map over a packed panel [2][nb][rows][Kp] FP32, box 32 x 128
@@ -413,18 +335,20 @@ CUtensorMap panel_map(float* base, long long nb, long long rows, long long Kp, i
   return m;
 }
 
-long long round_up(long long v, long long q) { return (v + q - 1) / q * q; }
-
 }  // namespace
 
-bool tc_eligible(const ContractDesc& d) {
-  // worth a tile of 128 x 128 and representable by the tensor maps; below 128
-  // of K (four slabs) the per-tile set-up and epilogue outweigh the MMAs, and
-  // the CUDA-core kernel is faster
+bool tc_shape_ok(const ContractDesc& d) {
+  // representable by the tensor maps and the grid; below 128 of K (four slabs)
+  // the per-tile set-up and epilogue outweigh the MMAs
   const long long kt = round_up(d.K, TC_BK) / 32;   // 32 x 32 pack tiles along k
   return d.M >= 64 && d.N >= 64 && d.K >= 128 && d.B <= 65535 &&
-         2.0 * d.B * d.M * d.N * d.K >= 1e8 && round_up(d.M, TC_BM) / TC_BM * (round_up(d.N, TC_BN) / TC_BN) < (1LL << 31) &&
+         round_up(d.M, TC_BM) / TC_BM * (round_up(d.N, TC_BN) / TC_BN) < (1LL << 31) &&
          kt * (round_up(std::max(d.M, d.N), TC_BM) / 32) < (1LL << 31);
+}
+
+bool tc_eligible(const ContractDesc& d) {
+  // worth a tile of 128 x 128: below 1e8 flops the CUDA-core kernel is faster
+  return tc_shape_ok(d) && 2.0 * d.B * d.M * d.N * d.K >= 1e8;
 }
 
 // K splits: only when the output has too few tiles to fill the GPU; at least
@@ -447,7 +371,7 @@ size_t tc_scratch_floats(const ContractDesc& d) {
 }
 
 void launch_contract_tc(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
-                        float* scratch, int* status) {
+                        float* scratch, int* status, unsigned long long wait_ns) {
   if (d.M == 0 || d.N == 0 || d.B == 0) return;
   const long long Kp = round_up(d.K, TC_BK), Mp = round_up(d.M, TC_BM), Np = round_up(d.N, TC_BN);
   float* pa = scratch;
@@ -503,7 +427,7 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
   {
     ProfScope ps(PF_TENSOR, s, 2.0 * d.B * d.M * d.N * d.K,
                  8.0 * d.B * Kp * (Mp + Np) + 8.0 * d.B * d.M * d.N * (d.beta != 0 ? 2 : 1));
-    tc_gemm_kernel<<<grid, TC_THREADS_V2, TC_SMEM, s>>>(mA, mB, e, nk, per, C, W, Mp, Np, status);
+    tc_gemm_kernel<<<grid, TC_THREADS_V2, TC_SMEM, s>>>(mA, mB, e, nk, per, C, W, Mp, Np, status, wait_ns);
     SCTM_CUDA(cudaGetLastError());
   }
   if (W) launch_splitk_finish(d, Mp, Np, W, C, s);

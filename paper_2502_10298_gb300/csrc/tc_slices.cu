@@ -1,0 +1,531 @@
+// Tensor-core contraction with BF16 digit slices (precision 4; sm_103a,
+// tcgen05 + TMA).
+//
+// C[b,m,n] = alpha * sum_k A[b,m,k] B[b,k,n] + beta * C[b,m,n] with FP64
+// operands in any strided layout (the ContractDesc of the CUDA-core kernel).
+//
+// The splitting follows the error-free transformation of matrix products of
+// Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59, 2012): every row of A
+// (column of B) is scaled by a power of two 2^e, e the smallest with
+// max |row| < 2^e, so that x = v / 2^e lies in (-1, 1); x is written as
+//     x = 2^-7 (d1 + 2^-8 d2 + 2^-16 d3 + 2^-24 d4) + O(2^-32),
+// with integer digits |d_i| <= 128 obtained by repeated rounding to nearest.
+// The four slices S_i = d_i 2^(-8(i-1)) are exact BF16 numbers.  A product of
+// two slices of levels a, b is an integer multiple of 2^(-8(a+b-2)) of
+// magnitude <= 2^14 2^(-8(a+b-2)), and the tensor core's FP32 accumulator
+// adds such terms without rounding as long as the exact sum fits 24 bits:
+//   level 0 (S1 S1):           512 terms of K, <= 2^23           exact
+//   level 1 (S1 S2 + S2 S1):   2 x 512 terms, <= 2^16 in 2^-8    exact
+//   levels 2-3 (seven pairs):  accumulated in FP32 with rounding; their
+//                              weight 2^-16 leaves < 1e-10 of the result
+// The dropped pairs (levels 4..6) and the digit remainder are O(2^-32) of
+// 2^(eA+eB) per product term.  Every 512 of K the three accumulators are read
+// out of tensor memory and added into double-float (two FP32) register sums
+// with an error-free two-sum, so no precision is lost across windows either.
+//
+// Three kernels: (1) the exponent of every operand row (max over K, by
+// atomicMax of the binary exponent); (2) pack: gather through the strides,
+// scale, split into the four slices, write a K-major BF16 panel
+// [slice][batch][rows][Kp]; (3) gemm: one 128 x 128 output tile per CTA, a
+// 3-stage ring of 32-wide K slabs (4 A + 4 B slices, 64 KB) filled by TMA with
+// 64-byte swizzle, ten tcgen05.mma kind::f16 per 16 of K, eight drain warps.
+//
+// Every mbarrier wait is bounded; on timeout the kernel records -2 in the
+// status word, waits (bounded) for what it issued, frees tensor memory and
+// returns.  The main-loop limit is a launch argument so that a test can make
+// the waits run out; the drain waits always keep the full limit.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "common.h"
+#include "kernels.h"
+#include "prof.h"
+#include "tcgen05_util.cuh"
+
+namespace sctm {
+
+using namespace tcx;
+
+namespace {
+
+constexpr int SL_NS = 4;                        // digit slices per operand
+constexpr int SL_BM = 128, SL_BN = 128;         // output tile
+constexpr int SL_BK = 32;                       // K slab: 32 BF16 = 64 bytes = one 64-byte swizzle row
+constexpr int SL_STAGES = 3;
+constexpr int SL_SLICE = SL_BM * SL_BK * 2;     // bytes of one slice of one slab (8 KB; BM == BN)
+constexpr int SL_STAGE = 2 * SL_NS * SL_SLICE;  // 64 KB
+constexpr int SL_SMEM = SL_STAGES * SL_STAGE + 1024;
+constexpr int SL_WINDOW = 16;                   // slabs (512 of K) per exact accumulation window
+constexpr int SL_DRAIN_WARPS = 8;
+constexpr int SL_THREADS = 64 + 32 * SL_DRAIN_WARPS;
+constexpr int SL_TMEM_COLS = 512;               // 3 x 128 accumulator columns, allocated as a power of two
+constexpr int kNoExp = (int)0x80808080;         // exponent of an all-zero row (memset pattern)
+static_assert(SL_BM == SL_BN, "slices of A and B share one size");
+static_assert(2 * SL_WINDOW * SL_BK * 64 <= (1 << 16), "level-1 window sums must stay exact in FP32");
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, rows of 64
+// bytes, 8-row atoms 512 bytes apart
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                    // leading-dimension offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;           // stride-dimension offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                    // descriptor version of tcgen05
+  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = 128
+constexpr uint32_t kIdescBF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SL_BN >> 3) << 17) |
+                                ((uint32_t)(SL_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdescBF16), "r"(accumulate)
+      : "memory");
+}
+
+// 2^n for -1022 <= n <= 1023, built from the exponent bits (exact)
+__device__ __forceinline__ double pow2_normal(int n) {
+  n = n < -1022 ? -1022 : (n > 1023 ? 1023 : n);
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
+// v 2^n for |n| <= 2044 in two exact steps (no library call in the hot loops)
+__device__ __forceinline__ double times_pow2(double v, int n) {
+  const int n1 = n / 2;
+  return v * pow2_normal(n1) * pow2_normal(n - n1);
+}
+
+// One operand seen as rows x k through its strides (batch b on grid y).
+struct SlicePack {
+  Group bat, rows, k;          // strides of the operand in .sa
+  long long nb, R, K, Rp, Kp;
+  int k_inner;                 // 1 when the operand is contiguous along k
+};
+
+// 32 x 32 tile of the operand, gathered so that both the strided read and the
+// shared-memory write are coalesced; zero outside the operand.
+__device__ __forceinline__ void gather_tile(const SlicePack& p, const double* __restrict__ X, long long r0,
+                                            long long k0, long long b, double (*tile)[33], long long* offR,
+                                            long long* offK) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  if (tid < 32) {
+    long long r = r0 + tid;
+    offR[tid] = r < p.R ? group_offset(p.rows, p.rows.sa, r) : -1;
+  } else if (tid < 64) {
+    long long k = k0 + tid - 32;
+    offK[tid - 32] = k < p.K ? group_offset(p.k, p.k.sa, k) : -1;
+  }
+  const long long ob = group_offset(p.bat, p.bat.sa, b);
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    int rr = p.k_inner ? i : tx, kk = p.k_inner ? tx : i;
+    long long orr = offR[rr], ok = offK[kk];
+    tile[rr][kk] = (orr >= 0 && ok >= 0) ? X[ob + orr + ok] : 0.0;
+  }
+  __syncthreads();
+}
+
+// expo[b][r] = max over k of (binary exponent of |X[b, r, k]| + 1), i.e. the
+// smallest e with |X[b, r, k]| < 2^e; kNoExp (the initial value) for a zero row.
+__global__ void __launch_bounds__(256) slice_exponent_kernel(SlicePack p, const double* __restrict__ X,
+                                                            int* __restrict__ expo) {
+  __shared__ long long offR[32], offK[32];
+  __shared__ double tile[32][33];
+  const long long nkt = p.Kp / 32, t = blockIdx.x;
+  const long long k0 = (t % nkt) * 32, r0 = (t / nkt) * 32, b = blockIdx.y;
+  gather_tile(p, X, r0, k0, b, tile, offR, offK);
+  // warp ty reduces rows ty, ty + 8, ...: lane tx holds column tx
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    double v = fabs(tile[i][threadIdx.x]);
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0 && v > 0.0 && r0 + i < p.R) atomicMax(&expo[b * p.Rp + r0 + i], ilogb(v) + 1);
+  }
+}
+
+// Four BF16 slices per value: panel[slice][b][r][k] (as raw 16-bit words).
+__global__ void __launch_bounds__(256) slice_pack_kernel(SlicePack p, const double* __restrict__ X,
+                                                        const int* __restrict__ expo, uint16_t* __restrict__ out) {
+  __shared__ long long offR[32], offK[32];
+  __shared__ double tile[32][33];
+  const long long nkt = p.Kp / 32, t = blockIdx.x;
+  const long long k0 = (t % nkt) * 32, r0 = (t / nkt) * 32, b = blockIdx.y;
+  gather_tile(p, X, r0, k0, b, tile, offR, offK);
+  const long long plane = p.nb * p.Rp * p.Kp;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int e = expo[b * p.Rp + r0 + i];
+    double x = e == kNoExp ? 0.0 : times_pow2(tile[i][threadIdx.x], -e);   // |x| < 1, exact
+    double r = x * 128.0;
+    float dig[SL_NS];
+#pragma unroll
+    for (int s = 0; s < SL_NS; ++s) {
+      const double d = rint(r);          // |d| <= 128
+      r = (r - d) * 256.0;               // exact: |r - d| <= 1/2
+      dig[s] = ldexpf((float)d, -8 * s);   // exact
+    }
+    const long long o = (b * p.Rp + r0 + i) * p.Kp + k0 + threadIdx.x;
+#pragma unroll
+    for (int s = 0; s < SL_NS; ++s) out[s * plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn(dig[s]));
+  }
+}
+
+struct SlEpi {
+  Group bat, m, n;             // output strides in .sc
+  long long M, N, Mp, Np;
+  double alpha, beta;
+  int num_m, num_n;            // tiles
+};
+
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+// Warp roles: warp 0 lane 0 issues TMA, warp 1 owns tensor memory and its
+// lane 0 issues the MMAs, warps 2..9 drain the accumulators.  Tensor memory
+// columns [0,128) level 0, [128,256) level 1, [256,384) levels 2 and 3.
+__global__ void __launch_bounds__(SL_THREADS, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, SlEpi e,
+                      const int* __restrict__ expA, const int* __restrict__ expB, int nk_total, int slabs_per_split,
+                      double* __restrict__ C, double* __restrict__ W, int* status, unsigned long long wait_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[SL_STAGES], empty[SL_STAGES], acc_full, acc_empty, done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int issued_parity[SL_STAGES];
+  __shared__ long long offCm[SL_BM], offCn[SL_BN];
+  __shared__ int eRow[SL_BM], eCol[SL_BN];
+
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.y;
+  // grouped raster: 8 row tiles share their B panels in L2
+  const int t = blockIdx.x, GM = 8;
+  const int group = t / (GM * e.num_n), first_m = group * GM;
+  const int gsz = min(e.num_m - first_m, GM);
+  const int m_tile = first_m + (t % (GM * e.num_n)) % gsz;
+  const int n_tile = (t % (GM * e.num_n)) / gsz;
+  const long long m0 = (long long)m_tile * SL_BM, n0 = (long long)n_tile * SL_BN;
+  const int s0 = blockIdx.z * slabs_per_split;
+  const int nk = min(nk_total - s0, slabs_per_split);
+
+  if (tid == 0) {
+    for (int s = 0; s < SL_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      issued_parity[s] = -1;
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, SL_DRAIN_WARPS);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(SL_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  const long long boC = group_offset(e.bat, e.bat.sc, b);
+  for (int i = tid; i < SL_BM; i += blockDim.x) {
+    long long m = m0 + i;
+    offCm[i] = m < e.M ? boC + group_offset(e.m, e.m.sc, m) : -1;
+    eRow[i] = expA[(long long)b * e.Mp + m0 + i];
+  }
+  for (int i = tid; i < SL_BN; i += blockDim.x) {
+    long long n = n0 + i;
+    offCn[i] = n < e.N ? group_offset(e.n, e.n.sc, n) : -1;
+    eCol[i] = expB[(long long)b * e.Np + n0 + i];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* ab = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: TMA slabs (four A slices, four B slices) into the ring
+      for (int s = 0; s < nk && !*ab; ++s) {
+        const int st = s % SL_STAGES;
+        if (s >= SL_STAGES && !mbar_wait(&empty[st], ((s / SL_STAGES) - 1) & 1, ab, wait_ns)) break;
+        uint8_t* sp = base + st * SL_STAGE;
+        mbar_expect_tx(&full[st], SL_STAGE);
+        issued_parity[st] = (s / SL_STAGES) & 1;
+        const int kc = (s0 + s) * SL_BK;
+#pragma unroll
+        for (int i = 0; i < SL_NS; ++i) {
+          tma_load_4d(sp + i * SL_SLICE, &mapA, &full[st], kc, (int)m0, b, i);
+          tma_load_4d(sp + (SL_NS + i) * SL_SLICE, &mapB, &full[st], kc, (int)n0, b, i);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: window w = s / SL_WINDOW accumulates afresh
+      for (int s = 0; s < nk; ++s) {
+        const int st = s % SL_STAGES, w = s / SL_WINDOW;
+        const bool first = (s % SL_WINDOW) == 0;
+        const bool last = (s % SL_WINDOW) == SL_WINDOW - 1 || s == nk - 1;
+        if (!mbar_wait(&full[st], (s / SL_STAGES) & 1, ab, wait_ns)) break;
+        if (first && w >= 1 && !mbar_wait(&acc_empty, (w - 1) & 1, ab, wait_ns)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d0 = tmem, d1 = tmem + 128, d2 = tmem + 256;
+        const uint32_t sa = smem_addr(base + st * SL_STAGE);
+        uint64_t a[SL_NS], bb[SL_NS];
+#pragma unroll
+        for (int i = 0; i < SL_NS; ++i) {
+          a[i] = desc_sw64(sa + i * SL_SLICE);
+          bb[i] = desc_sw64(sa + (SL_NS + i) * SL_SLICE);
+        }
+#pragma unroll
+        for (int kk = 0; kk < SL_BK / 16; ++kk) {
+          const uint64_t adv = (uint64_t)(kk * 16 * 2) >> 4;   // 16 BF16 values = 32 bytes along K
+          const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
+          mma_bf16(d0, a[0] + adv, bb[0] + adv, acc0);                    // level 0
+          mma_bf16(d1, a[0] + adv, bb[1] + adv, acc0);                    // level 1
+          mma_bf16(d1, a[1] + adv, bb[0] + adv, 1u);
+          mma_bf16(d2, a[0] + adv, bb[2] + adv, acc0);                    // level 2
+          mma_bf16(d2, a[1] + adv, bb[1] + adv, 1u);
+          mma_bf16(d2, a[2] + adv, bb[0] + adv, 1u);
+          mma_bf16(d2, a[0] + adv, bb[3] + adv, 1u);                      // level 3
+          mma_bf16(d2, a[1] + adv, bb[2] + adv, 1u);
+          mma_bf16(d2, a[2] + adv, bb[1] + adv, 1u);
+          mma_bf16(d2, a[3] + adv, bb[0] + adv, 1u);
+        }
+        mma_commit(&empty[st]);              // the slab's shared memory is free once these complete
+        if (last) mma_commit(&acc_full);     // the window's sums are ready
+      }
+      mma_commit(&done_bar);                 // tracks every MMA issued; waited before TMEM is freed
+      mbar_wait_bounded(&done_bar, 0);
+    }
+    __syncwarp();
+  } else {
+    // drain warps: rows 32 (warp % 4) + lane, columns 64 g .. 64 g + 63
+    const int q = warp & 3, g = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    // running double-float sums: hi in registers, lo in tensor-memory columns
+    // 384..511, which no MMA writes (64 more registers per thread would spill)
+    float hi[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) hi[j] = 0.f;
+    bool ok = true;
+    const int nwin = (nk + SL_WINDOW - 1) / SL_WINDOW;
+    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 64);
+    for (int w = 0; w < nwin; ++w) {
+      if (!mbar_wait(&acc_full, w & 1, ab, wait_ns)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        uint32_t v0[8], v1[8], v2[8], vl[8];
+        SCTM_TMEM_LD8(tb + h * 8, v0);
+        SCTM_TMEM_LD8(tb + 128 + h * 8, v1);
+        SCTM_TMEM_LD8(tb + 256 + h * 8, v2);
+        if (w > 0) SCTM_TMEM_LD8(tb + 384 + h * 8, vl);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float lo = w > 0 ? __uint_as_float(vl[j]) : 0.f;
+          two_sum_into(hi[h * 8 + j], lo, __uint_as_float(v0[j]));
+          two_sum_into(hi[h * 8 + j], lo, __uint_as_float(v1[j]));
+          lo += __uint_as_float(v2[j]);
+          vl[j] = __float_as_uint(lo);
+        }
+        SCTM_TMEM_ST8(tb + 384 + h * 8, vl);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty);
+    }
+    // stage the scaled tile in the (now idle) ring: every MMA has completed and
+    // every TMA copy has landed before the last window's sums were ready
+    double* tile = reinterpret_cast<double*>(base);   // [SL_BM][SL_BN + 1]
+    if (ok && !*ab) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int er = eRow[row];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        uint32_t vl[8];
+        SCTM_TMEM_LD8(tb + 384 + h * 8, vl);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = g * 64 + h * 8 + j, ec = eCol[c];
+          const double v = (double)hi[h * 8 + j] + (double)__uint_as_float(vl[j]);
+          tile[row * (SL_BN + 1) + c] = (er == kNoExp || ec == kNoExp) ? 0.0 : times_pow2(v, er + ec - 14);
+        }
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * SL_DRAIN_WARPS) : "memory");
+    if (!*ab) {
+      const int dt = tid - 64;
+      for (int idx = dt; idx < SL_BM * SL_BN; idx += 32 * SL_DRAIN_WARPS) {
+        const int r = idx / SL_BN, cn = idx % SL_BN;
+        const long long oc = offCm[r], on = offCn[cn];
+        if (oc < 0 || on < 0) continue;
+        if (W) {
+          // partial sum of this K range; splitk_finish_kernel applies alpha, beta
+          atomicAdd(&W[((long long)b * e.Mp + m0 + r) * e.Np + n0 + cn], tile[r * (SL_BN + 1) + cn]);
+          continue;
+        }
+        double v = e.alpha * tile[r * (SL_BN + 1) + cn];
+        if (e.beta != 0.0) v += e.beta * C[oc + on];
+        C[oc + on] = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*ab) {
+    // drain: wait (bounded, full limit) for the TMA copies and MMAs this CTA issued
+    if (tid == 0) {
+      atomicExch(status, -2);
+      for (int st = 0; st < SL_STAGES; ++st)
+        if (issued_parity[st] >= 0) mbar_wait_bounded(&full[st], (uint32_t)issued_parity[st]);
+      mbar_wait_bounded(&done_bar, 0);
+    }
+    __syncthreads();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SL_TMEM_COLS) : "memory");
+  }
+}
+
+// tensor map over a slice panel [SL_NS][nb][rows][Kp] BF16, box 32 x 128
+CUtensorMap slice_map(uint16_t* base, long long nb, long long rows, long long Kp) {
+  CUtensorMap m;
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nb, (cuuint64_t)SL_NS};
+  cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)(rows * Kp * 2), (cuuint64_t)(nb * rows * Kp * 2)};
+  cuuint32_t box[4] = {SL_BK, (cuuint32_t)SL_BM, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  SCTM_CHECK(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed (slice panel)");
+  return m;
+}
+
+// K splits: only when the output has too few tiles to fill the GPU; at least
+// one window (512 of K) per split
+int slice_splits(const ContractDesc& d) {
+  const long long tiles = (round_up(d.M, SL_BM) / SL_BM) * (round_up(d.N, SL_BN) / SL_BN) * d.B;
+  const long long nk = round_up(d.K, SL_BK) / SL_BK;
+  const long long want = (2 * kNumSMs + tiles - 1) / tiles;
+  long long sp = std::min<long long>(want, nk / SL_WINDOW);
+  if (sp < 2) return 1;
+  const long long per = (nk + sp - 1) / sp;
+  return (int)((nk + per - 1) / per);
+}
+
+struct SliceLayout {
+  long long Kp, Mp, Np;
+  size_t panelA, panelB, expA, expB, W, total;   // byte offsets
+};
+
+SliceLayout slice_layout(const ContractDesc& d) {
+  SliceLayout L;
+  L.Kp = round_up(d.K, SL_BK), L.Mp = round_up(d.M, SL_BM), L.Np = round_up(d.N, SL_BN);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = (size_t)round_up((long long)(o + bytes), 256);
+    return at;
+  };
+  L.panelA = take((size_t)SL_NS * d.B * L.Mp * L.Kp * 2);
+  L.panelB = take((size_t)SL_NS * d.B * L.Np * L.Kp * 2);
+  L.expA = take((size_t)d.B * L.Mp * 4);
+  L.expB = take((size_t)d.B * L.Np * 4);
+  L.W = slice_splits(d) > 1 ? take((size_t)d.B * L.Mp * L.Np * 8) : 0;
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+size_t slice_scratch_bytes(const ContractDesc& d) { return slice_layout(d).total + 256; }
+
+void launch_contract_slices(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
+                            void* scratch, int* status, unsigned long long wait_ns) {
+  if (d.M == 0 || d.N == 0 || d.B == 0) return;
+  SCTM_CHECK(tc_shape_ok(d), "contraction shape not representable on the tensor cores");
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(scratch) + 255) & ~uintptr_t(255));
+  const SliceLayout L = slice_layout(d);
+  uint16_t* pa = reinterpret_cast<uint16_t*>(base + L.panelA);
+  uint16_t* pb = reinterpret_cast<uint16_t*>(base + L.panelB);
+  int* ea = reinterpret_cast<int*>(base + L.expA);
+  int* eb = reinterpret_cast<int*>(base + L.expB);
+  SlicePack pA;
+  pA.bat = d.bat, pA.rows = d.m, pA.k = d.k;
+  pA.nb = d.B, pA.R = d.M, pA.K = d.K, pA.Rp = L.Mp, pA.Kp = L.Kp, pA.k_inner = d.a_k_inner;
+  SlicePack pB;
+  pB.bat = d.bat, pB.rows = d.n, pB.k = d.k;
+  for (int i = 0; i < kMaxDims; ++i) {
+    pB.bat.sa[i] = d.bat.sb[i];
+    pB.rows.sa[i] = d.n.sb[i];
+    pB.k.sa[i] = d.k.sb[i];
+  }
+  pB.nb = d.B, pB.R = d.N, pB.K = d.K, pB.Rp = L.Np, pB.Kp = L.Kp, pB.k_inner = d.b_n_inner ? 0 : 1;
+  // exponents (two gathers), then the slices (two more); the panels are written once
+  SCTM_CUDA(cudaMemsetAsync(ea, 0x80, (size_t)d.B * L.Mp * 4, s));
+  SCTM_CUDA(cudaMemsetAsync(eb, 0x80, (size_t)d.B * L.Np * 4, s));
+  const dim3 gA((unsigned)((L.Kp / 32) * (L.Mp / 32)), (unsigned)d.B), gB((unsigned)((L.Kp / 32) * (L.Np / 32)), (unsigned)d.B);
+  {
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * (d.M + d.N) * d.K);
+    slice_exponent_kernel<<<gA, dim3(32, 8), 0, s>>>(pA, A, ea);
+    SCTM_CUDA(cudaGetLastError());
+    slice_exponent_kernel<<<gB, dim3(32, 8), 0, s>>>(pB, B, eb);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  {
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * (d.M + d.N) * d.K + 2.0 * SL_NS * d.B * L.Kp * (L.Mp + L.Np));
+    slice_pack_kernel<<<gA, dim3(32, 8), 0, s>>>(pA, A, ea, pa);
+    SCTM_CUDA(cudaGetLastError());
+    slice_pack_kernel<<<gB, dim3(32, 8), 0, s>>>(pB, B, eb, pb);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  CUtensorMap mA = slice_map(pa, d.B, L.Mp, L.Kp);
+  CUtensorMap mB = slice_map(pb, d.B, L.Np, L.Kp);
+  SlEpi e;
+  e.bat = d.bat, e.m = d.m, e.n = d.n;
+  e.M = d.M, e.N = d.N, e.Mp = L.Mp, e.Np = L.Np, e.alpha = d.alpha, e.beta = d.beta;
+  e.num_m = (int)(L.Mp / SL_BM), e.num_n = (int)(L.Np / SL_BN);
+  static bool attr = false;
+  if (!attr) {
+    SCTM_CUDA(cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SL_SMEM));
+    attr = true;
+  }
+  const int nk = (int)(L.Kp / SL_BK);
+  const int splits = slice_splits(d);
+  const int per = (nk + splits - 1) / splits;
+  double* W = nullptr;
+  if (splits > 1) {
+    W = reinterpret_cast<double*>(base + L.W);
+    SCTM_CUDA(cudaMemsetAsync(W, 0, (size_t)d.B * L.Mp * L.Np * sizeof(double), s));
+  }
+  dim3 grid((unsigned)((long long)e.num_m * e.num_n), (unsigned)d.B, (unsigned)splits);
+  // algorithmic work 2 B M N K (the tensor pipe executes ten BF16 products per
+  // multiply-add); bytes: the slice panels read once, the FP64 result written
+  {
+    ProfScope ps(PF_TENSOR, s, 2.0 * d.B * d.M * d.N * d.K,
+                 2.0 * SL_NS * d.B * L.Kp * (L.Mp + L.Np) + 8.0 * d.B * d.M * d.N * (d.beta != 0 ? 2 : 1));
+    slice_gemm_kernel<<<grid, SL_THREADS, SL_SMEM, s>>>(mA, mB, e, ea, eb, nk, per, C, W, status, wait_ns);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  if (W) launch_splitk_finish(d, L.Mp, L.Np, W, C, s);
+}
+
+}  // namespace sctm

@@ -69,20 +69,26 @@ struct Tensor {
 
 // Bump allocator over one device allocation.  Forward intermediates of a taped
 // region live until the region's reverse pass is done; mark/release frees them.
+// A second stack grows down from the top end (alloc_high): it holds data that
+// the forward pass leaves for the reverse pass, which consumes it last in,
+// first out.
 class Arena {
  public:
   Arena() = default;
   ~Arena();
   void reserve(size_t bytes);
   double* alloc(long long n);          // 256-byte aligned, uninitialised
+  double* alloc_high(long long n);     // from the top end, 256-byte aligned, uninitialised
   size_t mark() const { return top_; }
   void release(size_t m) { top_ = m; }
+  size_t mark_high() const { return hi_; }
+  void release_high(size_t m) { hi_ = m; }
   size_t capacity() const { return cap_; }
   size_t high_water() const { return high_; }
 
  private:
   char* base_ = nullptr;
-  size_t cap_ = 0, top_ = 0, high_ = 0;
+  size_t cap_ = 0, top_ = 0, hi_ = 0, high_ = 0;
 };
 
 struct Tape {

@@ -83,37 +83,60 @@ def test_d2_chi16_thirty_sweeps_energy(S):
     assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
 
 
+def _through_inner(X, inner_up, inner_dn, k, rest):
+    """P_dn P_up of teal (red) lives on alpha = (green (yellow) kept index, rest
+    of the wires); mapped back through the green (yellow) pair of the same band
+    it becomes an operator on the unprojected wires, independent of the basis
+    and signs of the inner kept space: [(m, r), (m', r')]"""
+    Xr = X.reshape(k, rest, k, rest)
+    C = torch.einsum("ak,krls,lb->arbs", inner_dn, Xr, inner_up)
+    m = inner_dn.shape[0]
+    return C.reshape(m * rest, m * rest)
+
+
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("colour", [0, 1, 2, 3])
-def test_projectors(S, colour):
-    """P_up / P_dn of the first left-move column at the initial environment."""
-    Lx, Ly, D, chi = 2, 2, 2, 8
+def test_projectors(S, colour, order):
+    """Projector pairs of the first left-move column at the initial environment:
+    singular values, and the product P_dn P_up element by element for every
+    colour.  Green and yellow compare P_dn P_up itself (independent of the
+    basis and signs of their kept space).  Teal and red compare it mapped back
+    through the green (yellow) pair their alpha index comes from, which
+    removes the dependence on the inner pair's basis.  The oracle grows the
+    environment leg of alpha while the GPU pads it to chi, so the oracle's
+    alpha is embedded into the padded one and the padding must stay zero.
+    order 1: the alternative yellow/red order of App. B."""
+    Lx, Ly, D, chi, p = 2, 2, 2, 8, 2
     A = _near(Lx, Ly, D, 0.4, seed=14)
     Ac = C.as_cell(A)
     rec = {}
-    C.split_column_projectors(Ac, C.initial_env(Ac, chi), 0, chi, record=rec)
+    C.split_column_projectors(Ac, C.initial_env(Ac, chi), 0, chi, record=rec, order=C.ORDERS[order])
     name = ["green", "teal", "yellow", "red"][colour]
-    up_o, dn_o, s_o = rec[name][0]
-    with S.SplitCTMRG(Lx, Ly, 2, D, chi) as s:
+    inner = {"teal": ("green", 0), "red": ("yellow", 2)}.get(name)
+    up_o, dn_o, s_o = (t.detach() for t in rec[name][0])
+    with S.SplitCTMRG(Lx, Ly, p, D, chi, projector_order=order) as s:
         s.init(torch.tensor(A, device="cuda"))
         up, dn, sv = s.projectors(0, 0, 0, colour)
-    k, a = up_o.shape
-    # the oracle keeps min(chi, n) rows with grown alpha; embed into the padded layout
-    assert np.allclose(sv[:len(s_o)], s_o.detach().numpy()[:chi], rtol=1e-9, atol=1e-12 * float(s_o[0]))
-    upg = up.cpu()
-    dng = dn.cpu()
-    # alpha of the oracle is the grown subset of the padded alpha: compare through P_up P_dn products
-    Po = (dn_o @ up_o).detach()
-    Pg = (dng @ upg)
-    na = Po.shape[0]
-    # gpu alpha index order: (E-wire padded to chi, ...); oracle alpha dims in the same order
-    shape_o = {0: (Ac[0][0].shape[1] ** 2, D), 1: None, 2: None, 3: None}
-    if colour == 0:
-        eo = C.initial_env(Ac, chi)[0][0]["T4b"].shape[0]
-        idx = (torch.arange(eo)[:, None] * D + torch.arange(D)[None, :]).reshape(-1)
-        assert torch.allclose(Pg[idx][:, idx], Po, atol=1e-9 * Po.abs().max())
-    else:
-        tr_o, tr_g = torch.trace(Po), torch.trace(Pg)
-        assert abs(float(tr_o - tr_g)) < 1e-9 * max(1.0, abs(float(tr_o)))
+        if inner:
+            iup, idn, _ = s.projectors(0, 0, 0, inner[1])
+    n = min(len(s_o), chi)
+    assert np.allclose(sv[:n], s_o.numpy()[:n], rtol=1e-9, atol=1e-12 * float(s_o[0]))
+    Po = dn_o @ up_o
+    Pg = dn.cpu() @ up.cpu()
+    if inner:
+        rest = Pg.shape[0] // chi                             # wires of alpha beside the inner index
+        iup_o, idn_o, _ = (t.detach() for t in rec[inner[0]][0])
+        Po = _through_inner(Po, iup_o, idn_o, iup_o.shape[0], rest)
+        Pg = _through_inner(Pg, iup.cpu(), idn.cpu(), chi, rest)
+    lead = Pg.shape[0] // chi                                 # alpha = (env leg padded to chi, lead)
+    e_o = Po.shape[0] // lead
+    idx = (torch.arange(e_o)[:, None] * lead + torch.arange(lead)[None, :]).reshape(-1)
+    assert torch.allclose(Pg[idx][:, idx], Po, rtol=0, atol=1e-9 * Po.abs().max()), name
+    rest_mask = torch.ones(Pg.shape[0], dtype=torch.bool)
+    rest_mask[idx] = False
+    if rest_mask.any():
+        pad = max(float(Pg[rest_mask].abs().max()), float(Pg[:, rest_mask].abs().max()))
+        assert pad <= 1e-12 * float(Po.abs().max()), (name, pad)
 
 
 @pytest.mark.parametrize("Lx,Ly,D,chi,sweeps", [(1, 1, 2, 8, 2), (2, 2, 2, 6, 1)])
@@ -127,6 +150,23 @@ def test_gradient_matches_oracle_autograd(S, Lx, Ly, D, chi, sweeps):
     eo = En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, sweeps), h, hd)
     eo.backward()
     assert abs(e - float(eo)) < 1e-10 * abs(float(eo))
+    rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
+    assert rel < 1e-7, rel
+
+
+def test_fp64_d4_chi32_2x2_energy_and_gradient(S):
+    """FP64 forward and reverse pass at the 2x2, D=4, chi=32 workload (random
+    seeded tensors, Heisenberg J=1, two sweeps) against the oracle's autograd:
+    energy to 1e-10 relative, gradient to 1e-7 (norm)."""
+    A, c = I.config("d4_chi32_2x2")
+    chi, sweeps = c["chi"], 2
+    with S.SplitCTMRG(2, 2, 2, c["D"], chi) as s:
+        e, g = s.energy_grad(torch.tensor(A, device="cuda"), sweeps, H, None)
+    Ao = torch.tensor(A).requires_grad_(True)
+    Ac = [[Ao[x, y] for y in range(2)] for x in range(2)]
+    eo = En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, sweeps), H, None)
+    eo.backward()
+    assert abs(e - float(eo.detach())) < 1e-10 * abs(float(eo.detach()))
     rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
     assert rel < 1e-7, rel
 
@@ -241,5 +281,36 @@ def test_conventional_ctmrg_gradient_matches_oracle(S):
     eo = En.energy_per_site(Ac, C.conv_ctmrg(Ac, chi, sweeps), HR, None, split=False)
     eo.backward()
     assert abs(e - float(eo)) < 1e-10 * abs(float(eo))
+    rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
+    assert rel < 1e-7, rel
+
+
+@pytest.mark.parametrize("Lx,Ly,D,chi", [(1, 1, 2, 8), (2, 2, 2, 8)])
+def test_alternative_order_sweeps_environment_and_energy(S, Lx, Ly, D, chi):
+    """The alternative yellow/red order of App. B (projector_order 1) against
+    the oracle's: environment after three sweeps to 1e-8, energy to 1e-10."""
+    A = _near(Lx, Ly, D, 0.3, seed=13)
+    h, hd = (HR, None) if Lx == 1 else (H, 0.5 * H)
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, projector_order=1) as s:
+        s.init(torch.tensor(A, device="cuda"))
+        s.sweeps(3)
+        Ac = C.as_cell(A)
+        env = C.split_ctmrg(Ac, chi, 3, order="alternative")
+        assert env_max_rel_diff(s, env, chi) < 1e-8
+        e_gpu = s.energy(h, hd)
+        e_or = float(En.energy_per_site(Ac, env, h, hd))
+        assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
+
+
+def test_alternative_order_gradient_matches_oracle_autograd(S):
+    """Gradient through the alternative order, two sweeps, 1e-7 (norm)."""
+    Lx, Ly, D, chi, sweeps = 1, 1, 2, 8, 2
+    A = I.random_cell(Lx, Ly, 2, D, seed=3)
+    with S.SplitCTMRG(Lx, Ly, 2, D, chi, projector_order=1) as s:
+        e, g = s.energy_grad(torch.tensor(A, device="cuda"), sweeps, HR, None)
+    Ao = torch.tensor(A).requires_grad_(True)
+    eo = En.energy_per_site([[Ao[0, 0]]], C.split_ctmrg([[Ao[0, 0]]], chi, sweeps, order="alternative"), HR, None)
+    eo.backward()
+    assert abs(e - float(eo.detach())) < 1e-10 * abs(float(eo.detach()))
     rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
     assert rel < 1e-7, rel

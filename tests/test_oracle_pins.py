@@ -107,21 +107,26 @@ def _env_after(A, chi, sweeps):
     return Ac, C.split_ctmrg(Ac, chi=chi, sweeps=sweeps)
 
 
+@pytest.mark.parametrize("order", ["standard", "alternative"])
 @pytest.mark.parametrize("chi", [6, 40])
-def test_projector_identities(chi):
-    """For every colour: P_up P_dn = 1 on the kept space, P_dn P_up idempotent,
-    and rho^B P_dn P_up rho^T equals the best rank-chi approximation of M
-    (Eckart-Young: the residual is the norm of the discarded singular values)."""
+def test_projector_identities(chi, order):
+    """For every colour, in both yellow/red orders (App. B): P_up P_dn = 1 on
+    the kept space, P_dn P_up idempotent, and rho^B P_dn P_up rho^T equals the
+    best rank-chi approximation of M (Eckart-Young: the residual is the norm of
+    the discarded singular values)."""
     A = I.random_cell(2, 2, 2, 2, seed=7)
     Ac, env = _env_after(A, chi, 1)
     rec = {}
-    E, a, K, Pg, Py, Pt, Pr, E2, a2 = C.split_column_projectors(Ac, env, 0, chi, record=rec)
+    E, a, K, Pg, Py, Pt, Pr, E2, a2 = C.split_column_projectors(Ac, env, 0, chi, record=rec, order=order)
+    alt = order == "alternative"
     rhos = {
         "green": (C.green_rhoT(E[0], a[0]), C.green_rhoB(E[1], a[1])),
-        "yellow": (C.yellow_rhoT(E[0], a[0]), C.yellow_rhoB(E[0], a[0])),
+        "yellow": ((C.yellow_alt_rhoT(E[0], a[0]), C.yellow_alt_rhoB(E[0], a[0])) if alt else
+                   (C.yellow_rhoT(E[0], a[0]), C.yellow_rhoB(E[0], a[0]))),
         "teal": (C.teal_rhoT(E[0], a[0], K[0], E2[0], a2[0]),
                  C.teal_rhoB(E[1], a[1], K[1], E2[1], a2[1])),
-        "red": (C.red_rhoT(E[0], K[0], E2[0], a2[0]), C.red_rhoB(E[0], a[0], K[0], E2[0], a2[0])),
+        "red": ((C.red_alt_rhoT(E[0], K[0], E2[0], a2[0]), C.red_alt_rhoB(E[0], a[0], K[0], E2[0], a2[0])) if alt
+                else (C.red_rhoT(E[0], K[0], E2[0], a2[0]), C.red_rhoB(E[0], a[0], K[0], E2[0], a2[0]))),
     }
     for colour, (rT, rB) in rhos.items():
         up, dn, s = rec[colour][0]
@@ -467,3 +472,39 @@ def test_projector_pair_reduced_and_plain_forms_agree_on_rank_deficient_halves()
     fd = (fval(h) - fval(-h)) / (2 * h)
     an = float((Xg.grad * dX).sum() + (Yg.grad * dY).sum())
     assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+# ------------------------------------ alternative yellow/red order (App. B)
+def test_alternative_order_exact_states():
+    """The alternative order (physical leg truncated by yellow) on states the
+    CTMRG must reproduce exactly: Neel (-1/2 + J2/2 per site) and products of
+    generic entangled two-site states (state-vector energy)."""
+    phis = np.zeros((2, 2, 2))
+    phis[0, 0, 0] = phis[1, 1, 0] = phis[0, 1, 1] = phis[1, 0, 1] = 1.0
+    Ac = C.as_cell(I.product_state_cell(phis, D=2))
+    e = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, 4, 2, order="alternative"), H, 0.5 * H))
+    assert abs(e - (-0.5 + 0.25)) < 1e-12
+    for vertical in (False, True):
+        rng = np.random.default_rng(12 + vertical)
+        psis = rng.standard_normal((2, 2, 2))
+        Ac = C.as_cell(I.gauge_transform_cell(I.dimer_pairs_cell(psis, D=2, vertical=vertical), seed=3))
+        ref = SV.dimer_pairs_energy(psis, H, 0.5 * H, vertical=vertical)
+        e = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, 16, 3, order="alternative"), H, 0.5 * H))
+        assert abs(e - ref) < 1e-10, (vertical, e, ref)
+
+
+def test_alternative_order_agrees_with_standard_as_chi_grows():
+    """App. B's alternative order changes only which projector truncates the
+    physical leg, so at converged chi it must give the standard order's (and
+    the conventional CTMRG's) energy: on a random D=2 state after 40 steps the
+    differences shrink with chi and are below 2e-7 at chi = 24."""
+    Ac = C.as_cell(I.random_cell(1, 1, 2, 2, seed=0))
+    gaps = []
+    with torch.no_grad():
+        for chi in (8, 16, 24):
+            e_alt = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, 40, order="alternative"), HR))
+            e_std = float(En.energy_per_site(Ac, C.split_ctmrg(Ac, chi, 40), HR))
+            e_conv = float(En.energy_per_site(Ac, C.conv_ctmrg(Ac, chi, 40), HR, split=False))
+            gaps.append((abs(e_alt - e_conv), abs(e_alt - e_std)))
+    assert gaps[0][0] > gaps[1][0] > gaps[2][0], gaps
+    assert gaps[2][0] < 2e-7 and gaps[2][1] < 2e-7, gaps
