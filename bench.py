@@ -345,7 +345,11 @@ def main():
                          "form beside the mixed ones), precision 0 first for the gradient reference")
     ap.add_argument("--cutoff", type=float, default=1e-5, help="projector cutoff of --precisions")
     ap.add_argument("--oracle-energy", action="store_true", help="--precisions: also the oracle's forward energy")
+    ap.add_argument("--lbfgs", type=int, default=0,
+                    help="run the L-BFGS optimisation of the workload for this many energy+gradient evaluations")
     args = ap.parse_args()
+    if args.lbfgs:
+        return run_lbfgs(args)
     if args.precisions:
         return run_precisions(args)
     if args.impl == "reference":
@@ -554,20 +558,23 @@ def run_forward(args):
 
 def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8), p=2):
     """Device time of one directional move (mean over a sweep of four, after one
-    warm-up sweep) for the split and the conventional CTMRG at fixed chi, 1x1
-    cell, seeded N(0,1) tensor, mixed precision: the shape of the paper's
-    Fig. 5a (time of one absorption step against the bulk bond dimension)."""
+    warm-up sweep) for the split CTMRG in both yellow/red orders (App. B) and
+    the conventional CTMRG at fixed chi, 1x1 cell, seeded N(0,1) tensor, mixed
+    precision (--precision, default 1): the shape of the paper's Fig. 5a (time
+    of one absorption step against the bulk bond dimension)."""
     import torch
     import paper_2502_10298_gb300 as S
+    prec = args.precision if args.precision is not None else 1
     rows = []
     for D in Ds:
         A = I.random_cell(1, 1, p, D, seed=0)
         At = torch.tensor(A, device="cuda")
-        row = {"D": D, "chi": chi, "p": p}
-        for name, algo in (("split", 0), ("conventional", 1)):
+        row = {"D": D, "chi": chi, "p": p, "precision": prec}
+        for name, algo, order in (("split", 0, 0), ("split_alt_order", 0, 1), ("conventional", 1, 0)):
             n = chi * D * D
             ws = int(min(200 * 2**30, max(8 * 2**30, 40 * n * n * 8)))
-            with S.SplitCTMRG(1, 1, p, D, chi, precision=1, workspace_bytes=ws, algorithm=algo) as s:
+            with S.SplitCTMRG(1, 1, p, D, chi, precision=prec, workspace_bytes=ws, algorithm=algo,
+                              projector_order=order) as s:
                 s.init(At)
                 s.sweeps(1)
                 torch.cuda.synchronize()
@@ -630,6 +637,29 @@ def run_precisions(args):
                 "energy_err_vs_oracle": (e - e_or) if e_or is not None else None,
                 "grad_rel_err_vs_fp64_gpu": (float((g - g_ref).norm() / g_ref.norm()) if g_ref is not None else None)}
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_lbfgs(args):
+    """The variational loop of the workload: L-BFGS over energy_grad for a
+    fixed number of energy+gradient evaluations (10 for the D=8 workload),
+    from its seeded tensors.  Prints the energy trace and evals/s."""
+    import torch
+    import paper_2502_10298_gb300 as S
+    S.load_library()
+    A, c, h_nn, h_diag, sweeps, desc = workload(args.config, args.sweeps)
+    prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
+    At = torch.tensor(A, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, trace = S.lbfgs(At, c["chi"], sweeps, h_nn, h_diag, evaluations=args.lbfgs, precision=prec,
+                       workspace_bytes=args_ws(c, args.workspace_gb))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    print(json.dumps({"workload": desc, "precision": prec, "dtype": DTYPES[prec], "optimizer": "L-BFGS (strong Wolfe)",
+                      "evaluations": len(trace), "seconds": wall, "evals_per_s": len(trace) / wall,
+                      "energy_first": trace[0]["energy"], "energy_last": trace[-1]["energy"],
+                      "energy_best": min(t["energy"] for t in trace), "trace": trace}))
     return 0
 
 

@@ -13,8 +13,8 @@
  *    T3bra, T3ket, C4, T4bra, T4ket.  Every edge tensor is [previous, PEPS leg,
  *    next] along the clockwise chain C1 T1k T1b C2 T2k T2b C3 T3b T3k C4 T4b
  *    T4k; C2, C3, C4 are [previous, next] and C1 is [next (T1k), previous
- *    (T4k)].  Environment bonds (chi_E) and interlayer bonds (chi_I) are both
- *    chi and zero-padded to chi.
+ *    (T4k)].  Environment bonds have dimension chi_E = chi and interlayer
+ *    bonds chi_I (sctm_config.chi_I, by default chi), zero-padded to those.
  *  - Bond operators are real p^2 x p^2 matrices h[(t_i t_j), (s_i s_j)] with s
  *    the ket and t the bra physical index.
  *  - "dev" pointers are device pointers owned by the caller; "host" pointers
@@ -100,6 +100,12 @@ typedef struct {
                             [previous, ket leg, bra leg, next] (chi x D x D x chi) and
                             the same calls (init, move, energy_2x2, energy_grad) apply;
                             ctmrg_projectors is not available for it                */
+  int chi_I;             /* split CTMRG: interlayer bond dimension chi_I between a ket
+                            and a bra edge (Sec. II.B; 0: chi_I = chi, the paper's
+                            choice); chi is then chi_E.  Edges are [chi_E, D, chi_I]
+                            (T1k, T2k, T3b, T4b) and [chi_I, D, chi_E] (T1b, T2b, T3k,
+                            T4k); green and teal keep chi_E values, yellow, red and
+                            the initial edge split chi_I                              */
   int projector_order;   /* split CTMRG: 0 = the physical leg of the ket is truncated
                             by the red projectors (Sec. II.B, App. A); 1 = by the
                             yellow ones (the alternative order of App. B, which
@@ -145,10 +151,11 @@ SCTM_API int split_ctmrg_run(sctm_handle h, int max_sweeps, double tol, int* swe
 /* Projector pair of one cut of the move `dir` at the current environment,
  * without moving.  colour: 0 green, 1 teal, 2 yellow, 3 red (Sec. II.B, App. A).
  * (x, y) is the site in the frame of the move (the left-move frame is the
- * lattice itself).  P_up_dev: [chi][alpha], P_dn_dev: [alpha][chi] with
- * alpha = chi*D (green, teal; yellow in order 0; red in order 1), chi*p*D
- * (red in order 0: [chi][p][D]) or chi*D*p (yellow in order 1: [chi][D][p]);
- * s_host receives the chi largest singular values of the decomposed core. */
+ * lattice itself).  P_up_dev: [k][alpha], P_dn_dev: [alpha][k] with k = chi_E
+ * (green, teal) or chi_I (yellow, red) and alpha = k*D (green, teal; yellow in
+ * order 0; red in order 1), k*p*D (red in order 0: [k][p][D]) or k*D*p (yellow
+ * in order 1: [k][D][p]); s_host receives the k largest singular values of
+ * the decomposed core. */
 SCTM_API int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P_up_dev, double* P_dn_dev,
                      double* s_host);
 
@@ -184,8 +191,9 @@ SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int swee
 /* Environment of site (x, y) (the split environment of Fig. 2, Sec. II.B; for
  * the conventional algorithm the environment of Fig. 1, Sec. II.A) into
  * out_dev (device, caller-owned), packed in the order C1 T1k T1b C2
- * T2k T2b C3 T3b T3k C4 T4b T4k (chi^2 or chi*D*chi doubles each); for the
- * conventional algorithm C1 T1 C2 T2 C3 T3 C4 T4 (chi^2 or chi*D*D*chi each). */
+ * T2k T2b C3 T3b T3k C4 T4b T4k (chi_E^2 doubles per corner, chi_E*D*chi_I per
+ * edge, shapes as in sctm_config.chi_I); for the conventional algorithm C1 T1
+ * C2 T2 C3 T3 C4 T4 (chi^2 or chi*D*D*chi each). */
 SCTM_API int sctm_get_env(sctm_handle h, int x, int y, double* out_dev);
 
 /* Singular value decomposition M = U diag(S) V^T of an m x n row-major

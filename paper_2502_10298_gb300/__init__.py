@@ -7,3 +7,4 @@ in-tree library ``libsplitctmrg.so`` is missing: there is no fallback.
 """
 from .api import *  # noqa: F401,F403
 from .api import __all__  # noqa: F401
+from .optimize import lbfgs  # noqa: F401

@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
                 ("lorentz_eps", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("power_steps", ctypes.c_int), ("randomized_min", ctypes.c_int),
                 ("adjoint_cg_steps", ctypes.c_int), ("adjoint_band", ctypes.c_int),
-                ("rank_extra", ctypes.c_int), ("algorithm", ctypes.c_int), ("projector_order", ctypes.c_int)]
+                ("rank_extra", ctypes.c_int), ("algorithm", ctypes.c_int), ("chi_I", ctypes.c_int),
+                ("projector_order", ctypes.c_int)]
 
 
 _lib = None
@@ -93,10 +94,10 @@ def _hp(a):
 
 def sctm_create(Lx, Ly, p, D, chi, precision=0, svd_cutoff=0.0, lorentz_eps=0.0, workspace_bytes=0,
                 stream=None, power_steps=0, randomized_min=0, adjoint_cg_steps=0, adjoint_band=0, algorithm=0,
-                rank_extra=0, projector_order=0):
+                rank_extra=0, projector_order=0, chi_I=0):
     lib = load_library()
     cfg = Config(Lx, Ly, p, D, chi, precision, svd_cutoff, lorentz_eps, workspace_bytes, power_steps,
-                 randomized_min, adjoint_cg_steps, adjoint_band, rank_extra, algorithm, projector_order)
+                 randomized_min, adjoint_cg_steps, adjoint_band, rank_extra, algorithm, chi_I, projector_order)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     h = ctypes.c_void_p()
@@ -136,6 +137,8 @@ def split_ctmrg_run(h, max_sweeps: int, tol: float = 0.0):
 
 
 def ctmrg_projectors(h, direction, x, y, colour, chi, alpha):
+    """P_up [chi][alpha], P_dn [alpha][chi] and the chi kept singular values
+    (chi: chi_E for green and teal, chi_I for yellow and red)."""
     up = torch.empty((chi, alpha), dtype=torch.float64, device="cuda")
     dn = torch.empty((alpha, chi), dtype=torch.float64, device="cuda")
     s = np.zeros(chi)
@@ -172,14 +175,18 @@ def energy_grad_host(h, A_cell: np.ndarray, sweeps: int, h_nn, h_diag=None, grad
     return e.value, grad_out
 
 
-def sctm_get_env(h, x, y, chi, D, conventional=False):
+def sctm_get_env(h, x, y, chi, D, conventional=False, chi_I=None):
     """Environment of site (x, y): split keys (C1, T1k, T1b, ...) or, for the
-    conventional algorithm, C1, T1, C2, T2, C3, T3, C4, T4 with fused edges."""
+    conventional algorithm, C1, T1, C2, T2, C3, T3, C4, T4 with fused edges.
+    chi is chi_E; chi_I (default chi) the interlayer bond of the split edges."""
     keys = CONV_KEYS if conventional else ENV_KEYS
+    ci = chi if not chi_I else chi_I
     def shape(k):
         if k[0] == "C":
             return (chi, chi)
-        return (chi, D, D, chi) if conventional else (chi, D, chi)
+        if conventional:
+            return (chi, D, D, chi)
+        return (chi, D, ci) if k in ("T1k", "T2k", "T3b", "T4b") else (ci, D, chi)
     sizes = [int(np.prod(shape(k))) for k in keys]
     buf = torch.empty(sum(sizes), dtype=torch.float64, device="cuda")
     _check(h, _lib.sctm_get_env(h, x, y, _dev(buf)))
@@ -272,6 +279,7 @@ class SplitCTMRG:
         self.Lx, self.Ly, self.p, self.D, self.chi = Lx, Ly, p, D, chi
         self.conventional = kw.get("algorithm", 0) == 1
         self.order = kw.get("projector_order", 0)
+        self.chiI = kw.get("chi_I", 0) or chi
         self.h = sctm_create(Lx, Ly, p, D, chi, **kw)
 
     def close(self):
@@ -304,7 +312,7 @@ class SplitCTMRG:
         return split_ctmrg_run(self.h, max_sweeps, tol)
 
     def env(self, x, y):
-        return sctm_get_env(self.h, x, y, self.chi, self.D, self.conventional)
+        return sctm_get_env(self.h, x, y, self.chi, self.D, self.conventional, self.chiI)
 
     def energy(self, h_nn, h_diag=None):
         return energy_2x2(self.h, h_nn, h_diag)
@@ -315,5 +323,6 @@ class SplitCTMRG:
     def projectors(self, direction, x, y, colour):
         # the colour that carries the physical leg: red (order 0) or yellow (order 1)
         phys = (colour == 3) if self.order == 0 else (colour == 2)
-        alpha = self.chi * self.D * (self.p if phys else 1)
-        return ctmrg_projectors(self.h, direction, x, y, colour, self.chi, alpha)
+        k = self.chi if colour in (0, 1) else self.chiI      # green, teal: chi_E; yellow, red: chi_I
+        alpha = k * self.D * (self.p if phys else 1)
+        return ctmrg_projectors(self.h, direction, x, y, colour, k, alpha)

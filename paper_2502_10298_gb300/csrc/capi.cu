@@ -241,8 +241,11 @@ std::vector<double> corner_spectra(sctm_handle h) {
     const int nb = std::min(64, nc - b0);
     const size_t wn = svd_work_doubles(chi, chi, nb);
     double* work = wn ? h->c.arena.alloc((long long)wn) : nullptr;
+    // only the singular values are used: columns at rounding level (below
+    // 1e-14 of the largest, which a converged corner has many of) rotate but do
+    // not hold the sweeps back, and the orthogonality threshold is 1e-12
     launch_svd(chi, chi, nb, M + b0 * mm, U + b0 * mm, S + (long long)b0 * chi, V + b0 * mm, work,
-               h->c.svd_status, h->c.stream);
+               h->c.svd_status, h->c.stream, 1e-28, 1e-12);
   }
   check_svd(h);
   SCTM_CUDA(cudaMemcpyAsync(out.data(), S, out.size() * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
@@ -325,6 +328,9 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     SCTM_CHECK(cfg->precision >= 0 && cfg->precision <= 4, "precision must be 0 (FP64), 1, 2, 4 (mixed) or 3");
     Params& P = h->P;
     P.Lx = cfg->Lx, P.Ly = cfg->Ly, P.p = cfg->p, P.D = cfg->D, P.chi = cfg->chi;
+    SCTM_CHECK(cfg->chi_I >= 0, "chi_I must be >= 0");
+    P.chiI = cfg->chi_I > 0 ? cfg->chi_I : cfg->chi;
+    SCTM_CHECK(cfg->algorithm == 0 || P.chiI == P.chi, "chi_I applies to the split CTMRG only");
     P.mixed = (cfg->precision >= 1);   // randomized projectors for large truncated spaces
     h->c.fp32_compute = (cfg->precision == 1 || cfg->precision == 2 || cfg->precision == 4);
     h->c.tensor_cores = (cfg->precision == 1 || cfg->precision == 4);
@@ -350,7 +356,7 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     h->c.stream = (cudaStream_t)stream;
     SCTM_CHECK(cfg->algorithm == 0 || cfg->algorithm == 1, "algorithm must be 0 (split) or 1 (conventional)");
     P.conventional = (cfg->algorithm == 1);
-    const int chi = P.chi, D = P.D;
+    const int chi = P.chi, chiI = P.chiI, D = P.D;
     long long off = 0;
     for (int k = 0; k < NKEY; ++k) {
       bool corner = (k == C1 || k == C2 || k == C3 || k == C4);
@@ -369,8 +375,12 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
         h->key_shape[k][3] = chi;
         off += (long long)chi * D * D * chi;
       } else {
-        h->key_nd[k] = 3, h->key_shape[k][0] = chi, h->key_shape[k][1] = D, h->key_shape[k][2] = chi;
-        off += (long long)chi * D * chi;
+        // the first edge of a pair along the chain (T1k, T2k, T3b, T4b) is
+        // [chi_E, D, chi_I], the second (T1b, T2b, T3k, T4k) [chi_I, D, chi_E]
+        const bool first = (k == T1k || k == T2k || k == T3b || k == T4b);
+        h->key_nd[k] = 3, h->key_shape[k][0] = first ? chi : chiI, h->key_shape[k][1] = D;
+        h->key_shape[k][2] = first ? chiI : chi;
+        off += (long long)chi * D * chiI;
       }
     }
     h->env_site = off;
@@ -497,7 +507,8 @@ int ctmrg_projectors(sctm_handle h, int dir, int x, int y, int colour, double* P
     SCTM_CUDA(cudaMemcpyAsync(P_up_dev, pp.up.data, n * sizeof(double), cudaMemcpyDeviceToDevice, h->c.stream));
     SCTM_CUDA(cudaMemcpyAsync(P_dn_dev, pp.dn.data, n * sizeof(double), cudaMemcpyDeviceToDevice, h->c.stream));
     if (s_host)
-      SCTM_CUDA(cudaMemcpyAsync(s_host, pp.s.data, h->P.chi * sizeof(double), cudaMemcpyDeviceToHost, h->c.stream));
+      SCTM_CUDA(cudaMemcpyAsync(s_host, pp.s.data, pp.up.shape[0] * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->c.stream));
     SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
     h->c.arena.release(mk);
   });

@@ -286,9 +286,9 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
 // Mixed mode with alpha > 2 chi: the chi leading triplets of M come from a
 // randomized subspace iteration (randomized_svd_batch) and the reverse pass uses
 // the truncated-SVD adjoint above.
-static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, const Trunc& t) {
+static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, const Trunc& t,
+                                  int k) {
   AccurateScope acc(c);
-  const int k = P.chi;
   bool tap = c.tape.active;
   {
     // leaves U_r, S_r, V_r with gradient buffers when taping; the projector
@@ -326,26 +326,34 @@ static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, c
   }
 }
 
-static bool use_randomized(const Params& P, const Tensor& rhoT) {
+static bool use_randomized(const Params& P, const Tensor& rhoT, int k) {
   const int n = std::min(rhoT.shape[0], rhoT.shape[1]);
-  return P.mixed && n > P.chi + P.rank_extra && n >= P.randomized_min;
+  return P.mixed && n > k + P.rank_extra && n >= P.randomized_min;
 }
 
-std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB) {
+// Projector pairs of several cuts, pair i keeping ks[i] values; the randomized
+// decompositions of pairs with equal k run as one batch.
+std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB,
+                                 const std::vector<int>& ks) {
   std::vector<ProjPair> out(rT.size());
-  std::vector<int> ri;
-  std::vector<Tensor> bT, bB;
+  std::vector<int> kvals;
   for (size_t i = 0; i < rT.size(); ++i) {
-    if (use_randomized(P, rT[i])) {
-      ri.push_back((int)i);
-      bT.push_back(rT[i]);
-      bB.push_back(rB[i]);
-    } else {
-      out[i] = projector(c, P, rT[i], rB[i]);
+    if (!use_randomized(P, rT[i], ks[i])) {
+      out[i] = projector(c, P, rT[i], rB[i], ks[i]);
+    } else if (std::find(kvals.begin(), kvals.end(), ks[i]) == kvals.end()) {
+      kvals.push_back(ks[i]);
     }
   }
-  if (!ri.empty()) {
-    const int r = P.chi + P.rank_extra;
+  for (int k : kvals) {
+    std::vector<int> ri;
+    std::vector<Tensor> bT, bB;
+    for (size_t i = 0; i < rT.size(); ++i)
+      if (ks[i] == k && use_randomized(P, rT[i], k)) {
+        ri.push_back((int)i);
+        bT.push_back(rT[i]);
+        bB.push_back(rB[i]);
+      }
+    const int r = k + P.rank_extra;
     std::vector<Trunc> t(ri.size());
     Ctx::DecompCache& dc = c.decomp;
     if (dc.mode == 2) {
@@ -378,21 +386,20 @@ std::vector<ProjPair> projectors(Ctx& c, const Params& P, const std::vector<Tens
       }
       c.tape.active = tap;
     }
-    for (size_t j = 0; j < ri.size(); ++j) out[ri[j]] = finish_randomized(c, P, bT[j], bB[j], t[j]);
+    for (size_t j = 0; j < ri.size(); ++j) out[ri[j]] = finish_randomized(c, P, bT[j], bB[j], t[j], k);
   }
   return out;
 }
 
-ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB) {
+ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, int k) {
   const int a = rhoT.shape[0], b = rhoT.shape[1];
   SCTM_CHECK(rhoB.shape[0] == b && rhoB.shape[1] == a, "projector: rho shapes do not match");
-  const int k = P.chi;
-  if (use_randomized(P, rhoT)) {
+  if (use_randomized(P, rhoT, k)) {
     bool tap = c.tape.active;
     c.tape.active = false;
     Trunc t = randomized_svd_batch(c, {rhoT}, {rhoB}, k + P.rank_extra, P.power_steps)[0];
     c.tape.active = tap;
-    return finish_randomized(c, P, rhoT, rhoB, t);
+    return finish_randomized(c, P, rhoT, rhoB, t, k);
   }
   Tensor left, right;  // core = left @ right  (n x n), P_up = w U^T left, P_dn = right V w
   if (a < b) {
@@ -682,8 +689,11 @@ static ProjPair shaped(const ProjPair& p, int a0, int a1, int a2 = 0) {
 // ------------------------------------------------------------------ left move
 void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& out) {
   const int Lx = cell.Lx;
-  const int D = P.D, p = P.p, chi = P.chi;
+  const int D = P.D, p = P.p, chi = P.chi, chiI = P.chiI;
   out.g.resize(Lx); out.y.resize(Lx); out.t.resize(Lx); out.r.resize(Lx); out.K.resize(Lx);
+  // green and teal cut environment bonds (chi_E), yellow and red interlayer ones (chi_I)
+  std::vector<int> ks(2 * Lx, chi);
+  for (int x = 0; x < Lx; ++x) ks[Lx + x] = chiI;
   // ket stage: green (rows x | x+1) and yellow (row x) of every row, batched
   std::vector<Tensor> rT, rB;
   for (int x = 0; x < Lx; ++x) {
@@ -695,10 +705,10 @@ void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& o
     rT.push_back(alt ? yellow_alt_rhoT(c, cell.e(x, y), cell.a(x, y)) : yellow_rhoT(c, cell.e(x, y), cell.a(x, y)));
     rB.push_back(alt ? yellow_alt_rhoB(c, cell.e(x, y), cell.a(x, y)) : yellow_rhoB(c, cell.e(x, y), cell.a(x, y)));
   }
-  std::vector<ProjPair> pk = projectors(c, P, rT, rB);
+  std::vector<ProjPair> pk = projectors(c, P, rT, rB, ks);
   for (int x = 0; x < Lx; ++x) {
     out.g[x] = shaped(pk[x], chi, D);
-    out.y[x] = alt ? shaped(pk[Lx + x], chi, D, p) : shaped(pk[Lx + x], chi, D);
+    out.y[x] = alt ? shaped(pk[Lx + x], chiI, D, p) : shaped(pk[Lx + x], chiI, D);
   }
   for (int x = 0; x < Lx; ++x)
     out.K[x] = ket_stage(c, cell.e(x, y), cell.a(x, y), out.g[(x + Lx - 1) % Lx], out.y[x], out.g[x]);
@@ -719,10 +729,10 @@ void column_projectors(Ctx& c, const Params& P, Cell& cell, int y, ColumnProj& o
       rB.push_back(red_rhoB(c, cell.e(x, y), cell.a(x, y), out.K[x], cell.e(x, y + 1), cell.a(x, y + 1)));
     }
   }
-  std::vector<ProjPair> pb = projectors(c, P, rT, rB);
+  std::vector<ProjPair> pb = projectors(c, P, rT, rB, ks);
   for (int x = 0; x < Lx; ++x) {
     out.t[x] = shaped(pb[x], chi, D);
-    out.r[x] = alt ? shaped(pb[Lx + x], chi, D) : shaped(pb[Lx + x], chi, p, D);
+    out.r[x] = alt ? shaped(pb[Lx + x], chiI, D) : shaped(pb[Lx + x], chiI, p, D);
   }
 }
 
@@ -807,16 +817,16 @@ void move(Ctx& c, const Params& P, Cell& cell, int dir) {
 // ------------------------------------------------------------------ init
 // Split a conventional edge T[P,K,K2,N] (matrix (P K) x (K2 N)) into
 // first[P,K,i] = U sqrt(S) and second[i,K2,N] = sqrt(S) V^T, keeping
-// min(chi, rank) values above the cutoff, sign fixed on the columns of U,
-// zero-padded to [chi_P, K, chi] and [chi, K2, chi_N].
+// min(chi_I, rank) values above the cutoff, sign fixed on the columns of U,
+// zero-padded to [chi_P, K, chi_I] and [chi_I, K2, chi_N].
 // Split a double-layer edge T[prev, ket leg, bra leg, next] into its ket and
-// bra halves from the SVD of ((prev, ket), (bra, next)) truncated to chi:
-// first = U sqrt(S), second = sqrt(S) V^T, each zero-padded to chi.
+// bra halves from the SVD of ((prev, ket), (bra, next)) truncated to chi_I:
+// first = U sqrt(S), second = sqrt(S) V^T, each zero-padded (chi_E legs to chi_E).
 static void split_edge_from(Ctx& c, const Params& P, const Tensor& T, const SVDResult& r, Tensor& first,
                             Tensor& second, int padP, int padN) {
   const int Pd = T.shape[0], Kd = T.shape[1], K2 = T.shape[2], Nd = T.shape[3];
   const int rows = Pd * Kd;
-  const int k = std::min(P.chi, rows);
+  const int k = std::min(P.chiI, rows);
   Tensor q = spectrum_map(c, r.S, k, P.cutoff, 1);
   Tensor Uk = r.U, Vk = r.V;
   Uk.shape[1] = k;
@@ -824,8 +834,8 @@ static void split_edge_from(Ctx& c, const Params& P, const Tensor& T, const SVDR
   Tensor sg = row_signs(c, Uk.rev());     // sign of each U column
   Tensor Us = scale_dim(c, scale_dim(c, Uk, 1, q), 1, sg);
   Tensor Vs = scale_dim(c, scale_dim(c, Vk, 1, q), 1, sg);
-  first = c.zeros({padP, Kd, P.chi});
-  second = c.zeros({P.chi, K2, padN});
+  first = c.zeros({padP, Kd, P.chiI});
+  second = c.zeros({P.chiI, K2, padN});
   Tensor fv = first, sv = second;
   fv.shape[0] = Pd; fv.shape[2] = k;
   sv.shape[0] = k;  sv.shape[2] = Nd;
@@ -1225,7 +1235,7 @@ void conv_left_move(Ctx& c, const Params& P, Cell& cell) {
       rT[x] = einsum(c, "ra,rb->ab", TL, TR);   // alpha = TL's lower cut (n,d,e)  x  beta
       rB[x] = einsum(c, "al,bl->ab", BR, BL);   // beta x alpha
     }
-    std::vector<ProjPair> pp = projectors(c, P, rT, rB);
+    std::vector<ProjPair> pp = projectors(c, P, rT, rB, std::vector<int>(rT.size(), P.chi));
     const int n = cell.e(0, y)[T4k].shape[0];
     std::vector<std::array<Tensor, 3>> out(Lx);
     for (int x = 0; x < Lx; ++x) {

@@ -26,7 +26,9 @@ struct Cell {
 };
 
 struct Params {
-  int Lx = 1, Ly = 1, p = 2, D = 2, chi = 16;
+  int Lx = 1, Ly = 1, p = 2, D = 2;
+  int chi = 16;               // environment bond dimension chi_E (corners, environment legs of the edges)
+  int chiI = 16;              // interlayer bond dimension chi_I (between a ket and a bra edge)
   double cutoff = 1e-8;       // relative cutoff on the projector singular values
   double gram_cutoff = 1e-15; // relative cutoff on Gram eigenvalues (reduction)
   double eps_l = 1e-36;       // Lorentzian broadening (relative to s_max^4)
@@ -45,8 +47,9 @@ struct ProjPair {
   Tensor s;        // singular values of the decomposed core
 };
 
-// Projector pair from rhoT (alpha x beta) and rhoB (beta x alpha).
-ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB);
+// Projector pair from rhoT (alpha x beta) and rhoB (beta x alpha), keeping k
+// singular values (chi_E for green and teal, chi_I for yellow and red).
+ProjPair projector(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, int k);
 
 struct KetStage {
   // C1k[i,g] T4kk[g,r,y,s] T4bk[y,v,t] C4k[t,k]; in the alternative order

@@ -64,6 +64,7 @@ constexpr int SL_THREADS = 64 + 32 * SL_DRAIN_WARPS;
 constexpr int SL_TMEM_COLS = 512;               // 3 x 128 accumulator columns, allocated as a power of two
 constexpr int kNoExp = (int)0x80808080;         // exponent of an all-zero row (memset pattern)
 static_assert(SL_BM == SL_BN, "slices of A and B share one size");
+static_assert(SL_NS == 4, "the pack kernel writes four slices");
 static_assert(2 * SL_WINDOW * SL_BK * 64 <= (1 << 16), "level-1 window sums must stay exact in FP32");
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, rows of 64
@@ -132,8 +133,18 @@ __device__ __forceinline__ void gather_tile(const SlicePack& p, const double* __
   __syncthreads();
 }
 
-// expo[b][r] = max over k of (binary exponent of |X[b, r, k]| + 1), i.e. the
-// smallest e with |X[b, r, k]| < 2^e; kNoExp (the initial value) for a zero row.
+// Binary exponent e with |v| < 2^e (the exponent field minus 1022; subnormals
+// take -1022), or kNoExp for v = 0: integer work on the bits only, since every
+// FP64 instruction is expensive on this GPU.
+__device__ __forceinline__ int exponent_bound(double v) {
+  const long long bits = __double_as_longlong(v);
+  if ((bits & 0x7FFFFFFFFFFFFFFFLL) == 0) return kNoExp;
+  const int E = (int)((bits >> 52) & 0x7FF);
+  return E == 0 ? -1022 : E - 1022;
+}
+
+// expo[b][r] = max over k of exponent_bound(X[b, r, k]): the smallest e with
+// |X[b, r, k]| < 2^e for every k; kNoExp (the initial value) for a zero row.
 __global__ void __launch_bounds__(256) slice_exponent_kernel(SlicePack p, const double* __restrict__ X,
                                                             int* __restrict__ expo) {
   __shared__ long long offR[32], offK[32];
@@ -143,13 +154,17 @@ __global__ void __launch_bounds__(256) slice_exponent_kernel(SlicePack p, const 
   gather_tile(p, X, r0, k0, b, tile, offR, offK);
   // warp ty reduces rows ty, ty + 8, ...: lane tx holds column tx
   for (int i = threadIdx.y; i < 32; i += 8) {
-    double v = fabs(tile[i][threadIdx.x]);
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0 && v > 0.0 && r0 + i < p.R) atomicMax(&expo[b * p.Rp + r0 + i], ilogb(v) + 1);
+    const int e = __reduce_max_sync(0xffffffffu, exponent_bound(tile[i][threadIdx.x]));
+    if (threadIdx.x == 0 && e != kNoExp && r0 + i < p.R) atomicMax(&expo[b * p.Rp + r0 + i], e);
   }
 }
 
 // Four BF16 slices per value: panel[slice][b][r][k] (as raw 16-bit words).
+// With x = v / 2^e, X = round(x 2^38) is formed by shifting the mantissa (the
+// shift is at least 14 because |v| < 2^e), and the balanced base-256 digits
+// d1 = round(X / 2^31), d2 = round(r1 / 2^23), d3, d4 (each |d| <= 128) come
+// from arithmetic shifts of the remainders: x = 2^-7 (d1 + 2^-8 d2 + 2^-16 d3
+// + 2^-24 d4) + r with |r| <= 2^-32.  Integer arithmetic only.
 __global__ void __launch_bounds__(256) slice_pack_kernel(SlicePack p, const double* __restrict__ X,
                                                         const int* __restrict__ expo, uint16_t* __restrict__ out) {
   __shared__ long long offR[32], offK[32];
@@ -160,18 +175,28 @@ __global__ void __launch_bounds__(256) slice_pack_kernel(SlicePack p, const doub
   const long long plane = p.nb * p.Rp * p.Kp;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int e = expo[b * p.Rp + r0 + i];
-    double x = e == kNoExp ? 0.0 : times_pow2(tile[i][threadIdx.x], -e);   // |x| < 1, exact
-    double r = x * 128.0;
-    float dig[SL_NS];
-#pragma unroll
-    for (int s = 0; s < SL_NS; ++s) {
-      const double d = rint(r);          // |d| <= 128
-      r = (r - d) * 256.0;               // exact: |r - d| <= 1/2
-      dig[s] = ldexpf((float)d, -8 * s);   // exact
+    const long long bits = __double_as_longlong(tile[i][threadIdx.x]);
+    long long Xv = 0;
+    if (e != kNoExp && (bits & 0x7FFFFFFFFFFFFFFFLL) != 0) {
+      const int E = (int)((bits >> 52) & 0x7FF);
+      const long long mant = (bits & ((1LL << 52) - 1)) | (E != 0 ? (1LL << 52) : 0);
+      const int lsb = (E == 0 ? 1 : E) - 1075;        // v = mant 2^lsb
+      const int sh = e - 38 - lsb;                     // X = round(mant / 2^sh), sh >= 14
+      const long long mag = sh >= 64 ? 0 : (((mant >> (sh - 1)) + 1) >> 1);
+      Xv = bits < 0 ? -mag : mag;
     }
+    const long long d1 = (Xv + (1LL << 30)) >> 31;
+    long long r = Xv - (d1 << 31);
+    const long long d2 = (r + (1LL << 22)) >> 23;
+    r -= d2 << 23;
+    const long long d3 = (r + (1LL << 14)) >> 15;
+    r -= d3 << 15;
+    const long long d4 = (r + (1LL << 6)) >> 7;
     const long long o = (b * p.Rp + r0 + i) * p.Kp + k0 + threadIdx.x;
-#pragma unroll
-    for (int s = 0; s < SL_NS; ++s) out[s * plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn(dig[s]));
+    out[o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1));
+    out[plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d2 * 0x1p-8f));
+    out[2 * plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d3 * 0x1p-16f));
+    out[3 * plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d4 * 0x1p-24f));
   }
 }
 

@@ -154,3 +154,17 @@ def test_full_size_gradient_is_the_derivative_of_the_energy(S):
     fd = (ep - em) / (2 * step)
     assert abs(fd - gn) < 0.1 * gn, (fd, gn)
 
+
+def test_lbfgs_lowers_the_energy():
+    """The L-BFGS driver over energy_grad (2x2 cell, D=2, chi=8, Heisenberg,
+    two sweeps per evaluation) from a random state: after 12 evaluations the
+    best energy per site lies well below the first and above the bound of
+    -3/4 per bond (-3/2 per site with two bonds per site)."""
+    import paper_2502_10298_gb300 as S
+    A = torch.tensor(I.random_cell(2, 2, 2, 2, seed=4), device="cuda")
+    _, trace = S.lbfgs(A, 8, 2, I.heisenberg_bond(), None, evaluations=12)
+    e0 = trace[0]["energy"]
+    best = min(t["energy"] for t in trace)
+    assert len(trace) >= 8
+    assert best < e0 - 0.1, (e0, best)
+    assert best > -1.5

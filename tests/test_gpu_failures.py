@@ -37,8 +37,10 @@ def test_jacobi_sweep_limit_reports_no_convergence_and_handle_recovers(S):
         assert ei.value.code == -3
         S.sctm_set_limits(s.h, 0, -1.0)
         e1, g1 = s.energy_grad(A, 2, h)
-    assert abs(e1 - e0) <= 1e-14 * abs(e0)
-    assert float((g1 - g0).abs().max()) <= 1e-14 * float(g0.abs().max())
+    # the same call on a fresh handle: equal up to the summation order of the
+    # split-K atomics
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert float((g1 - g0).abs().max()) <= 1e-12 * float(g0.abs().max())
 
 
 @pytest.mark.parametrize("prec", [1, 4])

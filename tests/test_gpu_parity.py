@@ -314,3 +314,34 @@ def test_alternative_order_gradient_matches_oracle_autograd(S):
     assert abs(e - float(eo.detach())) < 1e-10 * abs(float(eo.detach()))
     rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
     assert rel < 1e-7, rel
+
+
+@pytest.mark.parametrize("Lx,Ly,D,chiE,chiI", [(1, 1, 2, 12, 8), (2, 2, 2, 10, 6)])
+def test_interlayer_dimension_environment_and_energy(S, Lx, Ly, D, chiE, chiI):
+    """chi_I below chi_E (the regime of the chi_I sweep in Sec. III): the
+    environment after three sweeps to 1e-8 and the energy to 1e-10 against the
+    oracle's (chi_E, chi_I) mode."""
+    A = _near(Lx, Ly, D, 0.3, seed=13)
+    h, hd = (HR, None) if Lx == 1 else (H, 0.5 * H)
+    with S.SplitCTMRG(Lx, Ly, 2, D, chiE, chi_I=chiI) as s:
+        s.init(torch.tensor(A, device="cuda"))
+        s.sweeps(3)
+        Ac = C.as_cell(A)
+        env = C.split_ctmrg(Ac, (chiE, chiI), 3)
+        assert env_max_rel_diff(s, env, chiE, chiI) < 1e-8
+        e_gpu = s.energy(h, hd)
+        e_or = float(En.energy_per_site(Ac, env, h, hd))
+        assert abs(e_gpu - e_or) < 1e-10 * abs(e_or)
+
+
+def test_interlayer_dimension_gradient_matches_oracle_autograd(S):
+    """Gradient with chi_I = 6 < chi_E = 10, two sweeps, 1e-7 (norm)."""
+    A = I.random_cell(1, 1, 2, 2, seed=3)
+    with S.SplitCTMRG(1, 1, 2, 2, 10, chi_I=6) as s:
+        e, g = s.energy_grad(torch.tensor(A, device="cuda"), 2, HR, None)
+    Ao = torch.tensor(A).requires_grad_(True)
+    eo = En.energy_per_site([[Ao[0, 0]]], C.split_ctmrg([[Ao[0, 0]]], (10, 6), 2), HR, None)
+    eo.backward()
+    assert abs(e - float(eo.detach())) < 1e-10 * abs(float(eo.detach()))
+    rel = float((g.cpu() - Ao.grad).norm() / Ao.grad.norm())
+    assert rel < 1e-7, rel
