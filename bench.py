@@ -29,6 +29,7 @@ import ipeps_inputs as I  # noqa: E402
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal (about 152 SMs x 2.07 GHz x 4 flop/clk/SM)
 TC_CORNER_DRAM_BYTES = 6.576915e9 + 0.52181376e9   # ncu, tc_gemm_kernel on one 8192^3 product
+SLICE_CORNER_DRAM_BYTES = 6.670281e9 + 0.521873e9  # ncu, slice_gemm_kernel on one 8192^3 product
 
 
 def load_peaks():
@@ -217,7 +218,10 @@ def roofline_of(fam, p, peaks, src, prec):
     if fam == "tensor" and prec == 4:
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                # DRAM bytes (read + write) of one 8192^3 enlarged-corner product from one
+                # ncu capture of the current kernel
+                "traffic": SLICE_CORNER_DRAM_BYTES,
+                "traffic_launch": "8192^3 corner product (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "kernel": "slice_gemm_kernel (BF16 digit-slice tcgen05 contraction)",
                 "peak_source": f"{src} bf16 sustained",
                 "tensor_pipe_frac": 10.0 * achieved / peak,

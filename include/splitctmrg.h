@@ -93,7 +93,7 @@ typedef struct {
                             first chi + n - 1 (the rest of the spectrum is treated
                             as the complement)                                      */
   int rank_extra;        /* mixed mode, randomized projectors: columns beyond chi in the
-                            sketch (0: max(32, chi / 2))                             */
+                            sketch (0: max(32, chi / 2); precision 4: max(32, chi))  */
   int algorithm;         /* 0: split CTMRG (Sec. II.B).  1: the conventional double-
                             layer CTMRG the paper compares against (Sec. III), with
                             2x2-patch projectors; its edges are the fused ket-bra pairs

@@ -59,10 +59,10 @@ def neel_biased_cell(p: int, D: int, seed: int = 0, bias: float = 0.5) -> np.nda
 WORKLOADS = {
     "d2_chi16_1x1": dict(Lx=1, Ly=1, p=2, D=2, chi=16, J2=0.0, rotated=True, sweeps=30),
     "d4_chi32_2x2": dict(Lx=2, Ly=2, p=2, D=4, chi=32, J2=0.0, rotated=False, sweeps=30),
-    "d6_chi72_2x2": dict(Lx=2, Ly=2, p=2, D=6, chi=72, J2=0.0, rotated=False, sweeps=20, bench_precision=1),
+    "d6_chi72_2x2": dict(Lx=2, Ly=2, p=2, D=6, chi=72, J2=0.0, rotated=False, sweeps=20, bench_precision=4),
     "d8_chi128_2x2_j1j2": dict(Lx=2, Ly=2, p=2, D=8, chi=128, J2=0.5, rotated=False, sweeps=10,
-                               bench_precision=1, neel=True),
-    "d10_chi200_1x1": dict(Lx=1, Ly=1, p=2, D=10, chi=200, J2=0.0, rotated=True, sweeps=10, bench_precision=1),
+                               bench_precision=4, neel=True),
+    "d10_chi200_1x1": dict(Lx=1, Ly=1, p=2, D=10, chi=200, J2=0.0, rotated=True, sweeps=10, bench_precision=4),
 }
 
 

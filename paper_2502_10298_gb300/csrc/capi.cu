@@ -270,45 +270,96 @@ void sweep_untaped(sctm_handle h) {
   }
 }
 
-// Energy per site, one 2x2 patch at a time; with `seed` the reverse pass of
-// every patch runs right after it (adjoints accumulate in the leaves' gradient
-// buffers), so only one patch's intermediates are ever held.
+// Energy per site, one 2x2 patch at a time.  With `seed` the reverse pass of
+// every patch runs right after it and accumulates into the leaves' gradient
+// buffers.  Only the enlarged corners are taped; the products
+// Htop(o1,o2) = TL(o1)^T TR(o2) and Hbot(o3,o4) = BL(o3) BR(o4)^T are plain
+// buffers, and their reverse pass is written out (no gradient buffers for them):
+//   E_p = sum_t w_t N_t / N0,  N_t = <Htop(k_t), Hbot(l_t)>,  N0 = <Htop(0,0), Hbot(0,0)>,
+//   Htop^(k) = sum_{t: k_t = k} (w_t / N0) Hbot(l_t) - [k = (0,0)] (E_p / N0) Hbot(0,0),
+//   Hbot^(l) = sum_{t: l_t = l} (w_t / N0) Htop(k_t) - [l = (0,0)] (E_p / N0) Htop(0,0),
+//   TL_bar(o1) += TR(o2) Htop^(o1,o2)^T,  TR_bar(o2) += TL(o1) Htop^(o1,o2),
+//   BL_bar(o3) += Hbot^(o3,o4) BR(o4),    BR_bar(o4) += Hbot^(o3,o4)^T BL(o3);
+// then the corners' tape carries the adjoints to the environment and A.
 double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed) {
   Ctx& c = h->c;
-  EnergyOps ops = energy_ops(c, h->P, hn, hd);
+  const Params& P = h->P;
+  EnergyOps ops = energy_ops(c, P, hn, hd);
+  const std::vector<PatchTerm> terms = patch_terms(ops, P.Lx * P.Ly);
+  typedef std::pair<int, int> Key;
+  std::vector<Key> tkeys{{0, 0}}, bkeys{{0, 0}};
+  for (const PatchTerm& t : terms) {
+    if (std::find(tkeys.begin(), tkeys.end(), Key(t.t1, t.t2)) == tkeys.end()) tkeys.push_back({t.t1, t.t2});
+    if (std::find(bkeys.begin(), bkeys.end(), Key(t.b1, t.b2)) == bkeys.end()) bkeys.push_back({t.b1, t.b2});
+  }
+  auto idx = [](const std::vector<Key>& v, Key k) { return (int)(std::find(v.begin(), v.end(), k) - v.begin()); };
+  auto plain = [](Tensor t) {
+    t.grad = nullptr;
+    return t;
+  };
+  auto gview = [](const Tensor& t) {
+    Tensor g = t;
+    g.data = t.grad;
+    g.grad = nullptr;
+    return g;
+  };
   double E = 0;
-  for (int x = 0; x < h->P.Lx; ++x)
-    for (int y = 0; y < h->P.Ly; ++y) {
+  for (int x = 0; x < P.Lx; ++x)
+    for (int y = 0; y < P.Ly; ++y) {
       size_t mk = c.arena.mark();
       const size_t tm = c.tape.mark();
-      std::vector<EnergyTerm> terms = energy_patch(c, h->P, h->cell, ops, x, y);
-      std::vector<double> nums(terms.size()), dens(terms.size());
-      for (size_t i = 0; i < terms.size(); ++i) {
-        SCTM_CUDA(cudaMemcpyAsync(&nums[i], terms[i].num.data, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-        SCTM_CUDA(cudaMemcpyAsync(&dens[i], terms[i].den.data, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-      }
+      const bool tap = c.tape.active;
+      PatchCorners K = patch_corners(c, P, h->cell, ops, terms, x, y);
+      c.tape.active = false;
+      std::vector<Tensor> Ht, Hb;
+      for (const Key& k : tkeys) Ht.push_back(einsum(c, "ra,rb->ab", plain(K.TL[k.first]), plain(K.TR[k.second])));
+      for (const Key& k : bkeys) Hb.push_back(einsum(c, "al,bl->ab", plain(K.BL[k.first]), plain(K.BR[k.second])));
+      std::vector<Tensor> dev(terms.size() + 1);
+      dev[0] = dot(c, Ht[0], Hb[0]);
+      for (size_t i = 0; i < terms.size(); ++i)
+        dev[i + 1] = dot(c, Ht[idx(tkeys, {terms[i].t1, terms[i].t2})], Hb[idx(bkeys, {terms[i].b1, terms[i].b2})]);
+      std::vector<double> v(dev.size());
+      for (size_t i = 0; i < dev.size(); ++i)
+        SCTM_CUDA(cudaMemcpyAsync(&v[i], dev[i].data, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
       SCTM_CUDA(cudaStreamSynchronize(c.stream));
-      for (size_t i = 0; i < terms.size(); ++i) E += terms[i].w * nums[i] / dens[i];
+      const double N0 = v[0];
+      double Ep = 0;
+      for (size_t i = 0; i < terms.size(); ++i) Ep += terms[i].w * v[i + 1] / N0;
+      E += Ep;
       if (seed) {
-        // dE/dnum = w/den ; dE/dden = -w num/den^2 (accumulated per shared den)
-        std::vector<std::pair<double*, double>> acc;
-        auto add = [&](double* p, double v) {
-          for (auto& a : acc)
-            if (a.first == p) { a.second += v; return; }
-          acc.push_back({p, v});
-        };
-        for (size_t i = 0; i < terms.size(); ++i) {
-          SCTM_CHECK(terms[i].num.grad && terms[i].den.grad, "energy terms without gradient buffers");
-          add(terms[i].num.grad, terms[i].w / dens[i]);
-          add(terms[i].den.grad, -terms[i].w * nums[i] / (dens[i] * dens[i]));
+        SCTM_CHECK(tap, "energy gradient without a tape");
+        const long long nn = Ht[0].numel();
+        // top products: Htop^(k), then the cotangents of TL(o1) and TR(o2)
+        for (size_t ik = 0; ik < tkeys.size(); ++ik) {
+          size_t m2 = c.arena.mark();
+          Tensor Hh = c.zeros({Ht[0].shape[0], Ht[0].shape[1]});
+          for (size_t i = 0; i < terms.size(); ++i)
+            if (Key(terms[i].t1, terms[i].t2) == tkeys[ik])
+              launch_axpy(nn, terms[i].w / N0, Hb[idx(bkeys, {terms[i].b1, terms[i].b2})].data, Hh.data, c.stream);
+          if (ik == 0) launch_axpy(nn, -Ep / N0, Hb[0].data, Hh.data, c.stream);
+          const Tensor& TL = K.TL[tkeys[ik].first];
+          const Tensor& TR = K.TR[tkeys[ik].second];
+          einsum_into(c, "rb,ab->ra", plain(TR), Hh, gview(TL), 1.0, 1.0, false);
+          einsum_into(c, "ra,ab->rb", plain(TL), Hh, gview(TR), 1.0, 1.0, false);
+          c.arena.release(m2);
         }
-        std::vector<double> hostv(acc.size());
-        for (size_t i = 0; i < acc.size(); ++i) hostv[i] = acc[i].second;
-        for (size_t i = 0; i < acc.size(); ++i)
-          SCTM_CUDA(cudaMemcpyAsync(acc[i].first, &hostv[i], sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        for (size_t il = 0; il < bkeys.size(); ++il) {
+          size_t m2 = c.arena.mark();
+          Tensor Hh = c.zeros({Hb[0].shape[0], Hb[0].shape[1]});
+          for (size_t i = 0; i < terms.size(); ++i)
+            if (Key(terms[i].b1, terms[i].b2) == bkeys[il])
+              launch_axpy(nn, terms[i].w / N0, Ht[idx(tkeys, {terms[i].t1, terms[i].t2})].data, Hh.data, c.stream);
+          if (il == 0) launch_axpy(nn, -Ep / N0, Ht[0].data, Hh.data, c.stream);
+          const Tensor& BL = K.BL[bkeys[il].first];
+          const Tensor& BR = K.BR[bkeys[il].second];
+          einsum_into(c, "ab,bl->al", Hh, plain(BR), gview(BL), 1.0, 1.0, false);
+          einsum_into(c, "ab,al->bl", Hh, plain(BL), gview(BR), 1.0, 1.0, false);
+          c.arena.release(m2);
+        }
+        c.tape.active = tap;
         c.tape.backward_from(tm);
-        SCTM_CUDA(cudaStreamSynchronize(c.stream));   // hostv must outlive the copies
       }
+      c.tape.active = tap;
       c.arena.release(mk);
     }
   if (!std::isfinite(E)) throw std::runtime_error("non-finite energy");
@@ -343,9 +394,14 @@ int sctm_create(const sctm_config* cfg, void* stream, sctm_handle* out) {
     if (cfg->power_steps > 0) P.power_steps = cfg->power_steps;
     if (cfg->randomized_min > 0) P.randomized_min = cfg->randomized_min;
     SCTM_CHECK(cfg->rank_extra >= 0, "rank_extra must be >= 0");
-    // sketch of chi + max(32, chi / 2) columns: at D=4, chi=64 the randomized
-    // FP64 gradient stays within 1e-4 of the exact one from chi + 32 on
-    P.rank_extra = cfg->rank_extra > 0 ? cfg->rank_extra : std::max(32, P.chi / 2);
+    // sketch of chi + max(32, chi / 2) columns (precision 4: chi + max(32, chi)).
+    // The reverse pass couples the kept triplets exactly to the computed ones
+    // and to the rest of the spectrum only to leading order, so the gradient
+    // depends on the sketch width: at D=6, chi=72 (2x2, 2 sweeps, cutoff 1e-5)
+    // it is 3.8e-4 from the exact one with chi + 36 columns and 7.4e-5 with
+    // chi + 72, at 5 % more time; at D=4, chi=64 both stay within 1e-4
+    P.rank_extra = cfg->rank_extra > 0 ? cfg->rank_extra
+                                       : (cfg->precision == 4 ? std::max(32, P.chi) : std::max(32, P.chi / 2));
     SCTM_CHECK(cfg->adjoint_cg_steps >= 0 && cfg->adjoint_cg_steps <= 64, "adjoint_cg_steps must be in [0, 64]");
     P.adjoint_cg_steps = cfg->adjoint_cg_steps;
     SCTM_CHECK(cfg->adjoint_band >= 0, "adjoint_band must be >= 0");

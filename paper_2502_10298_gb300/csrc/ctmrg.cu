@@ -65,6 +65,26 @@ struct AccurateScope {
   ~AccurateScope() { --c.accurate; }
 };
 
+// Operands used by many contractions of a scope (the rho halves of the
+// randomized projectors: the power iteration, the projector formation and the
+// reverse pass multiply each of them several times, in both orientations) are
+// packed for the slice kernel once per layout and kept in the arena's high
+// stack until the scope ends.  Their data must not change meanwhile.
+struct SliceKeepScope {
+  Ctx& c;
+  size_t hi, nkeep, npanels;
+  SliceKeepScope(Ctx& cx, const std::vector<Tensor>& keep)
+      : c(cx), hi(cx.arena.mark_high()), nkeep(cx.slice_keep.size()), npanels(cx.slice_panels.size()) {
+    if (c.bf16_slices)
+      for (const Tensor& t : keep) c.slice_keep.push_back(t.data);
+  }
+  ~SliceKeepScope() {
+    c.slice_keep.resize(nkeep);
+    c.slice_panels.resize(npanels);
+    c.arena.release_high(hi);
+  }
+};
+
 // G = Y^T Y in FP64.
 static Tensor gram64(Ctx& c, const Tensor& Y) {
   // r x r output with a long row sum: the contraction splits K over extra CTAs
@@ -104,6 +124,9 @@ struct Trunc {
 static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>& rT, const std::vector<Tensor>& rB,
                                                int r, int power_steps) {
   AccurateScope acc(c);
+  std::vector<Tensor> keep = rT;
+  keep.insert(keep.end(), rB.begin(), rB.end());
+  SliceKeepScope kept(c, keep);
   const size_t nb = rT.size();
   std::vector<Tensor> Y(nb);
   for (size_t i = 0; i < nb; ++i) {
@@ -173,6 +196,7 @@ static constexpr double kComplementMinRel = 1e-3;
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l, int cg_steps) {
   AccurateScope acc(c);
+  SliceKeepScope kept(c, {rhoT, rhoB});
   // FP64 arithmetic up to M_bar's factors: the complement terms divide
   // P U_bar by s_i, and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level
   // rounding of it, amplified by 1/s_i up to the inverse cutoff, swamps the
@@ -289,6 +313,7 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
 static ProjPair finish_randomized(Ctx& c, const Params& P, const Tensor& rhoT, const Tensor& rhoB, const Trunc& t,
                                   int k) {
   AccurateScope acc(c);
+  SliceKeepScope kept(c, {rhoT, rhoB});
   bool tap = c.tape.active;
   {
     // leaves U_r, S_r, V_r with gradient buffers when taping; the projector
@@ -916,7 +941,8 @@ void init_env(Ctx& c, const Params& P, Cell& cell) {
 // sum_k O_k (x) Q_k (operator Schmidt decomposition of a p^2 x p^2 matrix); the
 // 2x2 patch is contracted as four enlarged corners with the operator O of a
 // corner applied to its site (on the bra side, see half_TL).
-// Bond value = <H_top(o1,o2), H_bot(o3,o4)> / <H_top(I,I), H_bot(I,I)>.
+// Bond value = <H_top(o1,o2), H_bot(o3,o4)> / <H_top(I,I), H_bot(I,I)>; the
+// products H and the reverse pass through them live in the C-ABI driver.
 static void host_svd(int n, std::vector<double> a, std::vector<double>& U, std::vector<double>& S,
                      std::vector<double>& V) {
   // one-sided Jacobi on an n x n host matrix (bond operator, n = p^2)
@@ -1069,86 +1095,71 @@ EnergyOps energy_ops(Ctx& c, const Params& P, const double* h_nn, const double* 
   return E;
 }
 
-std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const EnergyOps& E, int x, int y) {
+std::vector<PatchTerm> patch_terms(const EnergyOps& E, int nsites) {
+  std::vector<PatchTerm> t;
+  const double inv_n = 1.0 / nsites;
+  // nearest-neighbour bonds, half weight each (every bond lies in two patches)
+  for (const auto& pr : E.nn) {
+    const int o = pr.a, q = pr.b;
+    const double w = 0.5 * inv_n * pr.w;
+    t.push_back({o, q, 0, 0, w});   // top    (TL, TR)
+    t.push_back({0, 0, o, q, w});   // bottom (BL, BR)
+    t.push_back({o, 0, q, 0, w});   // left   (TL, BL)
+    t.push_back({0, o, 0, q, w});   // right  (TR, BR)
+  }
+  for (const auto& pr : E.diag) {
+    const int o = pr.a, q = pr.b;
+    const double w = inv_n * pr.w;
+    t.push_back({o, 0, 0, q, w});   // TL - BR
+    t.push_back({0, o, q, 0, w});   // TR - BL
+  }
+  return t;
+}
+
+PatchCorners patch_corners(Ctx& c, const Params& P, Cell& cell, const EnergyOps& E,
+                           const std::vector<PatchTerm>& terms, int x, int y) {
   const std::vector<Tensor>& opd = E.op;
-  const std::vector<EnergyOps::Pair>& nnp = E.nn;
-  const std::vector<EnergyOps::Pair>& dgp = E.diag;
   const size_t nops = opd.size();
-  std::vector<EnergyTerm> terms;
-  const double inv_n = 1.0 / (cell.Lx * cell.Ly);
-  {
-      SiteEnv& eTL = cell.e(x, y);
-      SiteEnv& eTR = cell.e(x, y + 1);
-      SiteEnv& eBR = cell.e(x + 1, y + 1);
-      SiteEnv& eBL = cell.e(x + 1, y);
-      // conventional environments hold the fused edges already
-      auto fused = [&](const Tensor& a, const Tensor& b, const char* spec) {
-        return P.conventional ? a : fuse_edge(c, a, b, spec);
-      };
-      Tensor T1L = fused(eTL[T1k], eTL[T1b], "aui,iwc->auwc");
-      Tensor T4T = fused(eTL[T4b], eTL[T4k], "nvq,qlb->nvlb");
-      Tensor T1R = fused(eTR[T1k], eTR[T1b], "aui,iwc->auwc");
-      Tensor T2T = fused(eTR[T2k], eTR[T2b], "frj,jzg->frzg");
-      Tensor T2B = fused(eBR[T2k], eBR[T2b], "frj,jzg->frzg");
-      Tensor T3R = fused(eBR[T3b], eBR[T3k], "hek,kdm->hedm");
-      Tensor T3L = fused(eBL[T3b], eBL[T3k], "hek,kdm->hedm");
-      Tensor T4B = fused(eBL[T4b], eBL[T4k], "nvq,qlb->nvlb");
-      const Tensor& aTL = cell.a(x, y);
-      const Tensor& aTR = cell.a(x, y + 1);
-      const Tensor& aBR = cell.a(x + 1, y + 1);
-      const Tensor& aBL = cell.a(x + 1, y);
-      std::vector<Tensor> cTL(nops), cTR(nops), cBR(nops), cBL(nops);
-      Tensor hTL, hTR, hBR, hBL;   // operator-independent halves, built once
-      auto bra = [&](int o, const Tensor& a) { return o ? einsum(c, "ts,tuldr->suldr", opd[o], a) : a; };
-      auto kTL = [&](int o) -> Tensor& {
-        if (!hTL.data) hTL = half_TL(c, eTL[C1], T1L, T4T, aTL);
-        if (!cTL[o].data) cTL[o] = finish_TL(c, hTL, bra(o, aTL));
-        return cTL[o];
-      };
-      auto kTR = [&](int o) -> Tensor& {
-        if (!hTR.data) hTR = half_TR(c, T1R, eTR[C2], T2T, aTR);
-        if (!cTR[o].data) cTR[o] = finish_TR(c, hTR, bra(o, aTR));
-        return cTR[o];
-      };
-      auto kBR = [&](int o) -> Tensor& {
-        if (!hBR.data) hBR = half_BR(c, T2B, eBR[C3], T3R, aBR);
-        if (!cBR[o].data) cBR[o] = finish_BR(c, hBR, bra(o, aBR));
-        return cBR[o];
-      };
-      auto kBL = [&](int o) -> Tensor& {
-        if (!hBL.data) hBL = half_BL(c, T4B, eBL[C4], T3L, aBL);
-        if (!cBL[o].data) cBL[o] = finish_BL(c, hBL, bra(o, aBL));
-        return cBL[o];
-      };
-      std::map<std::pair<int, int>, Tensor> top, bot;
-      auto Htop = [&](int o1, int o2) -> Tensor& {
-        auto key = std::make_pair(o1, o2);
-        if (!top.count(key)) top[key] = einsum(c, "ra,rb->ab", kTL(o1), kTR(o2));
-        return top[key];
-      };
-      auto Hbot = [&](int o3, int o4) -> Tensor& {
-        auto key = std::make_pair(o3, o4);
-        if (!bot.count(key)) bot[key] = einsum(c, "al,bl->ab", kBL(o3), kBR(o4));
-        return bot[key];
-      };
-      Tensor den = dot(c, Htop(0, 0), Hbot(0, 0));
-      // nearest-neighbour bonds, half weight each (every bond lies in two patches)
-      for (auto& pr : nnp) {
-        int o = pr.a, q = pr.b;
-        double w = 0.5 * inv_n * pr.w;
-        terms.push_back({dot(c, Htop(o, q), Hbot(0, 0)), den, w});   // top    (TL, TR)
-        terms.push_back({dot(c, Htop(0, 0), Hbot(o, q)), den, w});   // bottom (BL, BR)
-        terms.push_back({dot(c, Htop(o, 0), Hbot(q, 0)), den, w});   // left   (TL, BL)
-        terms.push_back({dot(c, Htop(0, o), Hbot(0, q)), den, w});   // right  (TR, BR)
-      }
-      for (auto& pr : dgp) {
-        int o = pr.a, q = pr.b;
-        double w = inv_n * pr.w;
-        terms.push_back({dot(c, Htop(o, 0), Hbot(0, q)), den, w});   // TL - BR
-        terms.push_back({dot(c, Htop(0, o), Hbot(q, 0)), den, w});   // TR - BL
-      }
-    }
-  return terms;
+  SiteEnv& eTL = cell.e(x, y);
+  SiteEnv& eTR = cell.e(x, y + 1);
+  SiteEnv& eBR = cell.e(x + 1, y + 1);
+  SiteEnv& eBL = cell.e(x + 1, y);
+  // conventional environments hold the fused edges already
+  auto fused = [&](const Tensor& a, const Tensor& b, const char* spec) {
+    return P.conventional ? a : fuse_edge(c, a, b, spec);
+  };
+  Tensor T1L = fused(eTL[T1k], eTL[T1b], "aui,iwc->auwc");
+  Tensor T4T = fused(eTL[T4b], eTL[T4k], "nvq,qlb->nvlb");
+  Tensor T1R = fused(eTR[T1k], eTR[T1b], "aui,iwc->auwc");
+  Tensor T2T = fused(eTR[T2k], eTR[T2b], "frj,jzg->frzg");
+  Tensor T2B = fused(eBR[T2k], eBR[T2b], "frj,jzg->frzg");
+  Tensor T3R = fused(eBR[T3b], eBR[T3k], "hek,kdm->hedm");
+  Tensor T3L = fused(eBL[T3b], eBL[T3k], "hek,kdm->hedm");
+  Tensor T4B = fused(eBL[T4b], eBL[T4k], "nvq,qlb->nvlb");
+  const Tensor& aTL = cell.a(x, y);
+  const Tensor& aTR = cell.a(x, y + 1);
+  const Tensor& aBR = cell.a(x + 1, y + 1);
+  const Tensor& aBL = cell.a(x + 1, y);
+  std::vector<char> nTL(nops, 0), nTR(nops, 0), nBR(nops, 0), nBL(nops, 0);
+  nTL[0] = nTR[0] = nBR[0] = nBL[0] = 1;   // the norm <Htop(0,0), Hbot(0,0)>
+  for (const PatchTerm& t : terms) nTL[t.t1] = nTR[t.t2] = nBL[t.b1] = nBR[t.b2] = 1;
+  auto bra = [&](int o, const Tensor& a) { return o ? einsum(c, "ts,tuldr->suldr", opd[o], a) : a; };
+  PatchCorners K;
+  K.TL.resize(nops), K.TR.resize(nops), K.BR.resize(nops), K.BL.resize(nops);
+  // operator-independent halves, built once; the bra layer closes them
+  Tensor h = half_TL(c, eTL[C1], T1L, T4T, aTL);
+  for (size_t o = 0; o < nops; ++o)
+    if (nTL[o]) K.TL[o] = finish_TL(c, h, bra((int)o, aTL));
+  h = half_TR(c, T1R, eTR[C2], T2T, aTR);
+  for (size_t o = 0; o < nops; ++o)
+    if (nTR[o]) K.TR[o] = finish_TR(c, h, bra((int)o, aTR));
+  h = half_BR(c, T2B, eBR[C3], T3R, aBR);
+  for (size_t o = 0; o < nops; ++o)
+    if (nBR[o]) K.BR[o] = finish_BR(c, h, bra((int)o, aBR));
+  h = half_BL(c, T4B, eBL[C4], T3L, aBL);
+  for (size_t o = 0; o < nops; ++o)
+    if (nBL[o]) K.BL[o] = finish_BL(c, h, bra((int)o, aBL));
+  return K;
 }
 
 // ------------------------------------------------------------------ conventional CTMRG

@@ -81,10 +81,11 @@ void init_env(Ctx& c, const Params& P, Cell& cell);
 void conv_init_env(Ctx& c, const Params& P, Cell& cell);
 void conv_left_move(Ctx& c, const Params& P, Cell& cell);
 
-// energy pieces of one 2x2 patch: list of (numerator, denominator, weight),
-// E = sum over patches and terms of w * num / den
-struct EnergyTerm {
-  Tensor num, den;
+// Energy of one 2x2 patch: E_p = sum_t w_t <Htop(t1,t2), Hbot(b1,b2)> / <Htop(0,0), Hbot(0,0)>
+// with Htop(o1, o2) = TL(o1)^T TR(o2) and Hbot(o3, o4) = BL(o3) BR(o4)^T over the
+// enlarged corners of the patch, each carrying one operator slot o (0 = identity).
+struct PatchTerm {
+  int t1, t2, b1, b2;   // operator slots of TL, TR (top product) and BL, BR (bottom product)
   double w;
 };
 // bond operators split into one-site factors (operator-Schmidt decomposition);
@@ -95,7 +96,14 @@ struct EnergyOps {
   std::vector<Pair> nn, diag;
 };
 EnergyOps energy_ops(Ctx& c, const Params& P, const double* h_nn, const double* h_diag);
-// patch with top-left site (x, y)
-std::vector<EnergyTerm> energy_patch(Ctx& c, const Params& P, Cell& cell, const EnergyOps& E, int x, int y);
+// the bond terms of every patch (the same for all patches); nsites = Lx Ly
+std::vector<PatchTerm> patch_terms(const EnergyOps& E, int nsites);
+struct PatchCorners {
+  std::vector<Tensor> TL, TR, BR, BL;   // by operator slot; data == nullptr where no term needs it
+};
+// the enlarged corners of the patch with top-left site (x, y) that `terms`
+// need, taped when the tape is on
+PatchCorners patch_corners(Ctx& c, const Params& P, Cell& cell, const EnergyOps& E,
+                           const std::vector<PatchTerm>& terms, int x, int y);
 
 }  // namespace sctm

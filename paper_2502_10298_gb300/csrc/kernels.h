@@ -36,8 +36,20 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
 // two leading levels, FP64 output (tc_slices.cu).  Same eligibility as the
 // 3xTF32 form.  scratch: slice_scratch_bytes(d) bytes; status as above.
 size_t slice_scratch_bytes(const ContractDesc& d);
+// One operand packed for the slice kernel: the four BF16 slice panels
+// [slice][batch][rows padded to 128][K padded to 32] and the per-row exponents.
+struct SlicePanel {
+  uint16_t* panel = nullptr;
+  int* expo = nullptr;
+};
+// bytes (256-aligned start included) of operand A (b_operand false) or B of d, packed
+size_t slice_panel_bytes(const ContractDesc& d, bool b_operand);
+SlicePanel slice_pack(const ContractDesc& d, bool b_operand, const double* X, void* dst, cudaStream_t s);
+// preA / preB: operands packed beforehand (by slice_pack on a contraction with
+// the same operand layout); null = pack them here into the scratch
 void launch_contract_slices(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
-                            void* scratch, int* status, unsigned long long wait_ns = 2000000000ull);
+                            void* scratch, int* status, unsigned long long wait_ns = 2000000000ull,
+                            const SlicePanel* preA = nullptr, const SlicePanel* preB = nullptr);
 
 // deterministic N(0,1) test matrix (counter-based hash + Box-Muller), rows x cols
 void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s);

@@ -186,6 +186,29 @@ static ContractDesc plan(const Spec& sp, const Tensor& A, const Tensor& B, const
   return d;
 }
 
+// The packed slice panel of an operand whose data pointer the current scope
+// keeps (Ctx::slice_keep): packed into the arena's high stack on first use with
+// this layout, reused afterwards.  Null for operands that are not kept.
+static const SlicePanel* kept_slice_panel(Ctx& c, const ContractDesc& d, bool b_operand, const double* X,
+                                          SlicePanel& out) {
+  if (std::find(c.slice_keep.begin(), c.slice_keep.end(), X) == c.slice_keep.end()) return nullptr;
+  const Group& rows = b_operand ? d.n : d.m;
+  std::vector<long long> key{(long long)(uintptr_t)X, b_operand ? d.N : d.M, d.K, d.B};
+  for (const Group* g : {&d.bat, &rows, &d.k}) {
+    key.push_back(g->nd);
+    for (int i = 0; i < g->nd; ++i) key.push_back(g->size[i]), key.push_back(b_operand ? g->sb[i] : g->sa[i]);
+  }
+  for (const auto& e : c.slice_panels)
+    if (e.first == key) {
+      out = e.second;
+      return &out;
+    }
+  void* dst = c.arena.alloc_high((long long)(slice_panel_bytes(d, b_operand) + 7) / 8);
+  out = slice_pack(d, b_operand, X, dst, c.stream);
+  c.slice_panels.push_back({key, out});
+  return &out;
+}
+
 void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, const Tensor& C, double alpha,
                  double beta, bool record) {
   Spec sp = parse(spec);
@@ -204,8 +227,11 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
   if (c.fp32_compute && c.tensor_cores && (accurate ? tc_shape_ok(d) : tc_eligible(d))) {
     size_t mk = c.arena.mark();
     if (c.bf16_slices) {
+      SlicePanel pa, pb;
+      const SlicePanel* ppa = kept_slice_panel(c, d, false, A.data, pa);
+      const SlicePanel* ppb = kept_slice_panel(c, d, true, B.data, pb);
       void* scratch = c.arena.alloc((long long)(slice_scratch_bytes(d) + 7) / 8);
-      launch_contract_slices(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns);
+      launch_contract_slices(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns, ppa, ppb);
     } else {
       float* scratch = reinterpret_cast<float*>(c.arena.alloc((long long)(tc_scratch_floats(d) + 1) / 2));
       launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns);

@@ -32,6 +32,12 @@ struct Ctx {
     std::vector<std::array<Tensor, 3>> entries;
     size_t next = 0;
   } decomp;
+  // BF16-slice panels of operands that are reused while a scope runs (the rho
+  // halves of the randomized projectors): `slice_keep` lists their data
+  // pointers, `slice_panels` the panels packed so far (in the arena's high
+  // stack), keyed by the operand's layout in the contraction.
+  std::vector<const double*> slice_keep;
+  std::vector<std::pair<std::vector<long long>, SlicePanel>> slice_panels;
   int svd_max_sweeps = 60;       // Jacobi sweep limit (fault-injection hook: sctm_set_limits)
   unsigned long long pipe_wait_ns = 2000000000ull;   // tensor-core main-loop wait limit (same hook)
 

@@ -483,47 +483,64 @@ SliceLayout slice_layout(const ContractDesc& d) {
 
 size_t slice_scratch_bytes(const ContractDesc& d) { return slice_layout(d).total + 256; }
 
+namespace {
+SlicePack operand_pack(const ContractDesc& d, bool b_operand) {
+  const long long Kp = round_up(d.K, SL_BK);
+  SlicePack p;
+  if (!b_operand) {
+    p.bat = d.bat, p.rows = d.m, p.k = d.k;
+    p.nb = d.B, p.R = d.M, p.K = d.K, p.Rp = round_up(d.M, SL_BM), p.Kp = Kp, p.k_inner = d.a_k_inner;
+  } else {
+    p.bat = d.bat, p.rows = d.n, p.k = d.k;
+    for (int i = 0; i < kMaxDims; ++i) {
+      p.bat.sa[i] = d.bat.sb[i];
+      p.rows.sa[i] = d.n.sb[i];
+      p.k.sa[i] = d.k.sb[i];
+    }
+    p.nb = d.B, p.R = d.N, p.K = d.K, p.Rp = round_up(d.N, SL_BN), p.Kp = Kp, p.k_inner = d.b_n_inner ? 0 : 1;
+  }
+  return p;
+}
+}  // namespace
+
+size_t slice_panel_bytes(const ContractDesc& d, bool b_operand) {
+  const SlicePack p = operand_pack(d, b_operand);
+  return (size_t)round_up((long long)SL_NS * p.nb * p.Rp * p.Kp * 2, 256) + (size_t)p.nb * p.Rp * 4 + 256;
+}
+
+SlicePanel slice_pack(const ContractDesc& d, bool b_operand, const double* X, void* dst, cudaStream_t s) {
+  const SlicePack p = operand_pack(d, b_operand);
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dst) + 255) & ~uintptr_t(255));
+  SlicePanel out;
+  out.panel = reinterpret_cast<uint16_t*>(base);
+  out.expo = reinterpret_cast<int*>(base + round_up((long long)SL_NS * p.nb * p.Rp * p.Kp * 2, 256));
+  // exponents (one gather), then the slices (another); the panel is written once
+  SCTM_CUDA(cudaMemsetAsync(out.expo, 0x80, (size_t)p.nb * p.Rp * 4, s));
+  const dim3 g((unsigned)((p.Kp / 32) * (p.Rp / 32)), (unsigned)p.nb);
+  {
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K);
+    slice_exponent_kernel<<<g, dim3(32, 8), 0, s>>>(p, X, out.expo);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  {
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K + 2.0 * SL_NS * p.nb * p.Kp * p.Rp);
+    slice_pack_kernel<<<g, dim3(32, 8), 0, s>>>(p, X, out.expo, out.panel);
+    SCTM_CUDA(cudaGetLastError());
+  }
+  return out;
+}
+
 void launch_contract_slices(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
-                            void* scratch, int* status, unsigned long long wait_ns) {
+                            void* scratch, int* status, unsigned long long wait_ns, const SlicePanel* preA,
+                            const SlicePanel* preB) {
   if (d.M == 0 || d.N == 0 || d.B == 0) return;
   SCTM_CHECK(tc_shape_ok(d), "contraction shape not representable on the tensor cores");
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(scratch) + 255) & ~uintptr_t(255));
   const SliceLayout L = slice_layout(d);
-  uint16_t* pa = reinterpret_cast<uint16_t*>(base + L.panelA);
-  uint16_t* pb = reinterpret_cast<uint16_t*>(base + L.panelB);
-  int* ea = reinterpret_cast<int*>(base + L.expA);
-  int* eb = reinterpret_cast<int*>(base + L.expB);
-  SlicePack pA;
-  pA.bat = d.bat, pA.rows = d.m, pA.k = d.k;
-  pA.nb = d.B, pA.R = d.M, pA.K = d.K, pA.Rp = L.Mp, pA.Kp = L.Kp, pA.k_inner = d.a_k_inner;
-  SlicePack pB;
-  pB.bat = d.bat, pB.rows = d.n, pB.k = d.k;
-  for (int i = 0; i < kMaxDims; ++i) {
-    pB.bat.sa[i] = d.bat.sb[i];
-    pB.rows.sa[i] = d.n.sb[i];
-    pB.k.sa[i] = d.k.sb[i];
-  }
-  pB.nb = d.B, pB.R = d.N, pB.K = d.K, pB.Rp = L.Np, pB.Kp = L.Kp, pB.k_inner = d.b_n_inner ? 0 : 1;
-  // exponents (two gathers), then the slices (two more); the panels are written once
-  SCTM_CUDA(cudaMemsetAsync(ea, 0x80, (size_t)d.B * L.Mp * 4, s));
-  SCTM_CUDA(cudaMemsetAsync(eb, 0x80, (size_t)d.B * L.Np * 4, s));
-  const dim3 gA((unsigned)((L.Kp / 32) * (L.Mp / 32)), (unsigned)d.B), gB((unsigned)((L.Kp / 32) * (L.Np / 32)), (unsigned)d.B);
-  {
-    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * (d.M + d.N) * d.K);
-    slice_exponent_kernel<<<gA, dim3(32, 8), 0, s>>>(pA, A, ea);
-    SCTM_CUDA(cudaGetLastError());
-    slice_exponent_kernel<<<gB, dim3(32, 8), 0, s>>>(pB, B, eb);
-    SCTM_CUDA(cudaGetLastError());
-  }
-  {
-    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * (d.M + d.N) * d.K + 2.0 * SL_NS * d.B * L.Kp * (L.Mp + L.Np));
-    slice_pack_kernel<<<gA, dim3(32, 8), 0, s>>>(pA, A, ea, pa);
-    SCTM_CUDA(cudaGetLastError());
-    slice_pack_kernel<<<gB, dim3(32, 8), 0, s>>>(pB, B, eb, pb);
-    SCTM_CUDA(cudaGetLastError());
-  }
-  CUtensorMap mA = slice_map(pa, d.B, L.Mp, L.Kp);
-  CUtensorMap mB = slice_map(pb, d.B, L.Np, L.Kp);
+  const SlicePanel pa = preA ? *preA : slice_pack(d, false, A, base + L.panelA, s);
+  const SlicePanel pb = preB ? *preB : slice_pack(d, true, B, base + L.panelB, s);
+  CUtensorMap mA = slice_map(pa.panel, d.B, L.Mp, L.Kp);
+  CUtensorMap mB = slice_map(pb.panel, d.B, L.Np, L.Kp);
   SlEpi e;
   e.bat = d.bat, e.m = d.m, e.n = d.n;
   e.M = d.M, e.N = d.N, e.Mp = L.Mp, e.Np = L.Np, e.alpha = d.alpha, e.beta = d.beta;
@@ -547,7 +564,8 @@ void launch_contract_slices(const ContractDesc& d, const double* A, const double
   {
     ProfScope ps(PF_TENSOR, s, 2.0 * d.B * d.M * d.N * d.K,
                  2.0 * SL_NS * d.B * L.Kp * (L.Mp + L.Np) + 8.0 * d.B * d.M * d.N * (d.beta != 0 ? 2 : 1));
-    slice_gemm_kernel<<<grid, SL_THREADS, SL_SMEM, s>>>(mA, mB, e, ea, eb, nk, per, C, W, status, wait_ns);
+    slice_gemm_kernel<<<grid, SL_THREADS, SL_SMEM, s>>>(mA, mB, e, pa.expo, pb.expo, nk, per, C, W, status,
+                                                         wait_ns);
     SCTM_CUDA(cudaGetLastError());
   }
   if (W) launch_splitk_finish(d, L.Mp, L.Np, W, C, s);

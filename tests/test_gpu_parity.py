@@ -131,7 +131,11 @@ def test_projectors(S, colour, order):
     lead = Pg.shape[0] // chi                                 # alpha = (env leg padded to chi, lead)
     e_o = Po.shape[0] // lead
     idx = (torch.arange(e_o)[:, None] * lead + torch.arange(lead)[None, :]).reshape(-1)
-    assert torch.allclose(Pg[idx][:, idx], Po, rtol=0, atol=1e-9 * Po.abs().max()), name
+    # the product of one pair carries rounding amplified by s^-1/2 of values down
+    # to the 1e-8 cutoff; a composite multiplies three such products
+    tol = (1e-7 if inner else 1e-9) * float(Po.abs().max())
+    diff = float((Pg[idx][:, idx] - Po).abs().max())
+    assert diff <= tol, (name, diff, tol)
     rest_mask = torch.ones(Pg.shape[0], dtype=torch.bool)
     rest_mask[idx] = False
     if rest_mask.any():
