@@ -327,6 +327,7 @@ def main():
                     help="0 FP64, 1 mixed (3xTF32 tensor cores), 2 mixed on CUDA cores, 3 FP64 with randomized "
                          "projectors, 4 mixed with BF16 digit slices on the tensor cores; default per workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the kernels' split-K rules (no tuning)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--algorithm", default="split", choices=["split", "conventional"],
@@ -349,9 +350,17 @@ def main():
                          "form beside the mixed ones), precision 0 first for the gradient reference")
     ap.add_argument("--cutoff", type=float, default=1e-5, help="projector cutoff of --precisions")
     ap.add_argument("--oracle-energy", action="store_true", help="--precisions: also the oracle's forward energy")
+    ap.add_argument("--implicit", action="store_true",
+                    help="the implicit fixed-point gradient of the converged environment beside the checkpointed "
+                         "one (same precision): time, sweeps, solver iterations and peak workspace of each")
+    ap.add_argument("--near-product", type=float, default=None,
+                    help="--implicit: replace the workload's tensors by a near-product state of the same shape "
+                         "(0.8|0> + 0.6|1> on the zero bond index plus this much N(0,1) noise, seed 5)")
     ap.add_argument("--lbfgs", type=int, default=0,
                     help="run the L-BFGS optimisation of the workload for this many energy+gradient evaluations")
     args = ap.parse_args()
+    if args.implicit:
+        return run_implicit(args)
     if args.lbfgs:
         return run_lbfgs(args)
     if args.precisions:
@@ -396,10 +405,16 @@ def main():
     def step():
         return s.energy_grad(At, sweeps, h_nn, h_diag)
 
+    # the warm-up steps also run the split-K autotuner (each shape's candidates
+    # are complete contractions); the timed steps use its choices
+    if not args.no_autotune:
+        S.sctm_autotune(s.h, True)
     for _ in range(args.warmup):
         flush.zero_()
         step()
+    S.sctm_autotune(s.h, False)
     torch.cuda.synchronize()
+    tuned = S.sctm_autotune_table(s.h)
     if dist:
         dist.barrier()
     clk = ClockSampler(local)
@@ -477,6 +492,8 @@ def main():
             "data": "synthetic",
             "config": arm_config(desc, prec, world),
             "energy_per_site": e_val, "convergence_delta": conv_delta, "clocks": clocks, "e2e": e2e,
+            "autotune": {"shapes": len(tuned), "changed": sum(1 for r in tuned if r["chosen_splits"] != r["rule_splits"]),
+                         "ms_saved_per_call_sum": sum(r["rule_ms"] - r["chosen_ms"] for r in tuned)},
             "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu,
             "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
@@ -559,6 +576,57 @@ def run_forward(args):
                           "energy_per_site": e, "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}))
     return 0
 
+
+
+def run_implicit(args):
+    """Energy gradient of the converged environment two ways, in the handle's
+    precision: implicitly (energy_grad_implicit: run to the fixed point, one
+    step's reverse pass per adjoint iteration) and by the checkpointed reverse
+    pass through as many sweeps as the run took.  Reports seconds (CUDA events),
+    sweeps, solver iterations, the fixed-point check and the peak workspace of
+    each, and the relative difference of the two gradients.  A state whose
+    projector gauge is not fixed between steps is reported as refused."""
+    import torch
+    import paper_2502_10298_gb300 as S
+    A, c, h_nn, h_diag, _, desc = workload(args.config, args.sweeps)
+    if args.near_product is not None:
+        rng = np.random.default_rng(5)
+        A = np.zeros_like(A)
+        A[:, :, 0, 0, 0, 0, 0] = 0.8
+        A[:, :, 1, 0, 0, 0, 0] = 0.6
+        A = A + args.near_product * rng.standard_normal(A.shape)
+        desc += f" (near-product state, noise {args.near_product})"
+    prec = args.precision if args.precision is not None else c.get("bench_precision", 0)
+    At = torch.tensor(A, device="cuda")
+    ws = args_ws(c, args.workspace_gb)
+    out = {"workload": desc, "precision": prec, "dtype": DTYPES[prec]}
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        r = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return r, ev0.elapsed_time(ev1) / 1e3
+
+    g_imp = None
+    with S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec, workspace_bytes=ws) as s:
+        try:
+            (e, g_imp, info), sec = timed(lambda: s.energy_grad_implicit(At, h_nn, h_diag, max_sweeps=300))
+            out["implicit"] = {"seconds": sec, "energy_per_site": e, **info,
+                               "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
+        except S.SctmError as ex:
+            out["implicit"] = {"refused": str(ex)}
+    sweeps = out["implicit"].get("sweeps") or c["sweeps"]
+    with S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec, workspace_bytes=ws) as s:
+        (e, g), sec = timed(lambda: s.energy_grad(At, sweeps, h_nn, h_diag))
+        out["checkpointed"] = {"seconds": sec, "sweeps": sweeps, "energy_per_site": e,
+                               "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
+    if g_imp is not None:
+        out["grad_rel_diff"] = float((g_imp - g).norm() / g.norm())
+    print(json.dumps(out))
+    return 0
 
 def run_move_scaling(args, chi=128, Ds=(4, 5, 6, 7, 8), p=2):
     """Device time of one directional move (mean over a sweep of four, after one
@@ -670,11 +738,15 @@ def run_lbfgs(args):
 def args_ws(c, gb=None):
     """Device workspace: one taped 2x2 patch of the energy (about 220 enlarged-corner
     sized buffers of (chi D^2)^2 doubles, gradients included) plus a taped sweep."""
+    import torch
     if gb:
         return int(gb * 2**30)
     n = c["chi"] * c["D"] ** 2
     need = 220 * n * n * 8 + 16 * 2**30
-    return int(min(240 * 2**30, max(8 * 2**30, need)))
+    # at most the free device memory less 12 GiB (CUDA context, library state
+    # and the caller's tensors)
+    cap = torch.cuda.mem_get_info()[0] - 12 * 2**30 if torch.cuda.is_available() else 240 * 2**30
+    return int(min(cap, max(8 * 2**30, need)))
 
 
 if __name__ == "__main__":

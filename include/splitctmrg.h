@@ -46,7 +46,9 @@ enum {
   SCTM_ERR_SVD_NOCONV = -3,/* a Jacobi SVD did not converge                 */
   SCTM_ERR_NONFINITE = -4, /* NaN or Inf in a result                        */
   SCTM_ERR_OOM = -5,       /* device workspace too small                    */
-  SCTM_ERR_STATE = -6      /* call order (e.g. move before init)            */
+  SCTM_ERR_STATE = -6,     /* call order (e.g. move before init)            */
+  SCTM_ERR_NOT_FIXED_POINT = -7, /* environment not an element-wise fixed point */
+  SCTM_ERR_NO_CONVERGENCE = -8   /* an iteration reached its limit          */
 };
 
 typedef struct sctm_ctx* sctm_handle;
@@ -188,6 +190,32 @@ SCTM_API int energy_grad(sctm_handle h, const double* A_cell_dev, int sweeps, co
 SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const double* h_nn_host,
                      const double* h_diag_host, double* e_per_site, double* grad_host);
 
+/* Energy per site at the converged environment and its gradient by implicit
+ * differentiation of the fixed point env* = f(env*, A), f one full step of
+ * the four directional moves.  Sec. II.B iterates f until the environment
+ * converges and Sec. I / Sec. III differentiate the converged energy; the rule
+ * follows from the implicit function theorem:
+ *   dE/dA = dE/dA|env* + x^T df/dA|env*,  x = dE/denv* + x^T df/denv|env*.
+ * Steps: initial environment, full steps until the corner spectra change by
+ * less than tol (as split_ctmrg_run) or max_sweeps; one more step must change
+ * no entry of any environment tensor by more than fixed_point_tol of that
+ * tensor's largest entry, else SCTM_ERR_NOT_FIXED_POINT (the projector gauge
+ * is not fixed from step to step); the energy's reverse pass at env*; x by
+ * iterating its equation from x = dE/denv* until the change is below
+ * solve_tol of |x|, at most max_iter times, else
+ * SCTM_ERR_NO_CONVERGENCE; each iteration is one reverse pass through the
+ * step (its four moves recomputed from checkpoints, decompositions reused).
+ * Tolerances <= 0 take the defaults: tol 1e-13, fixed_point_tol 1e-9,
+ * solve_tol 1e-12 at precisions 0 and 3; 1e-7, 1e-5, 1e-6 in the precisions
+ * with FP32-level contractions (1, 2, 4).
+ * grad_dev (device, layout of A_cell) receives dE/dA.  Optional host outputs:
+ * sweeps_done, solver_iterations, fixed_point_change (the largest relative
+ * change of that extra step).  Leaves env* in the handle; synchronises. */
+SCTM_API int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps, double tol,
+                                  const double* h_nn_host, const double* h_diag_host, double fixed_point_tol,
+                                  double solve_tol, int max_iter, double* e_per_site, double* grad_dev,
+                                  int* sweeps_done, int* solver_iterations, double* fixed_point_change);
+
 /* Environment of site (x, y) (the split environment of Fig. 2, Sec. II.B; for
  * the conventional algorithm the environment of Fig. 1, Sec. II.A) into
  * out_dev (device, caller-owned), packed in the order C1 T1k T1b C2
@@ -245,6 +273,26 @@ SCTM_API int sctm_profile(sctm_handle h, int enable, double* out);
 
 /* Device workspace high-water mark in bytes. */
 SCTM_API int sctm_workspace_high_water(sctm_handle h, size_t* bytes);
+
+/* Split-K autotuning, the engine's own tuner (the paper has no counterpart).
+ * A contraction whose output has too few tiles to fill the GPU splits K over
+ * more CTAs, by a rule in each kernel.  enable = 1: from now on, the first
+ * calls of every such contraction shape (kernel, batch, M, N, K) run with the
+ * rule's split count, half and twice it, and no split -- one candidate per
+ * call, each a complete contraction, timed with events on the handle's stream
+ * (the calls synchronise while a shape is being explored) -- and later calls
+ * of that shape use the fastest.  enable = 0 stops exploring; shapes already
+ * tuned keep their choice for the handle's lifetime.  Errors: none beyond
+ * SCTM_ERR_ARG for a null handle. */
+SCTM_API int sctm_autotune(sctm_handle h, int enable);
+
+/* The tuner's choices: up to max_rows rows of nine doubles into out (host,
+ * caller-owned): kernel (0 FP64 CUDA cores, 1 FP32 CUDA cores, 2 3xTF32
+ * tensor cores, 3 BF16-slice tensor cores), batch, M, N, K, the rule's split
+ * count and its milliseconds, the chosen count and its milliseconds.  *rows
+ * receives the number of tuned shapes (which may exceed max_rows).
+ * Synchronises the stream. */
+SCTM_API int sctm_autotune_table(sctm_handle h, double* out, int max_rows, int* rows);
 
 /* Limits of the handle's bounded device loops, for fault-injection tests (the
  * paper has no counterpart).  svd_max_sweeps: sweeps of every Jacobi SVD the

@@ -10,7 +10,7 @@ import torch
 __all__ = [
     "load_library", "Config", "sctm_create", "sctm_destroy", "split_ctmrg_init", "split_ctmrg_move",
     "split_ctmrg_sweeps", "split_ctmrg_run", "ctmrg_projectors", "energy_2x2", "energy_grad", "energy_grad_host",
-    "sctm_get_env", "sctm_workspace_high_water", "sctm_set_limits", "sctm_profile", "sctm_svd", "sctm_svd_noalloc", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
+    "energy_grad_implicit", "sctm_get_env", "sctm_workspace_high_water", "sctm_set_limits", "sctm_autotune", "sctm_autotune_table", "sctm_profile", "sctm_svd", "sctm_svd_noalloc", "sctm_einsum", "SplitCTMRG", "ENV_KEYS", "SctmError",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsplitctmrg.so")
 ENV_KEYS = ("C1", "T1k", "T1b", "C2", "T2k", "T2b", "C3", "T3b", "T3k", "C4", "T4b", "T4k")
 CONV_KEYS = ("C1", "T1", "C2", "T2", "C3", "T3", "C4", "T4")
 _ERRORS = {-1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_SVD_NOCONV", -4: "ERR_NONFINITE", -5: "ERR_OOM",
-           -6: "ERR_STATE"}
+           -6: "ERR_STATE", -7: "ERR_NOT_FIXED_POINT", -8: "ERR_NO_CONVERGENCE"}
 
 
 class SctmError(RuntimeError):
@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH):
         "energy_2x2": (i, [vp, _dp, _dp, _dp]),
         "energy_grad": (i, [vp, vp, i, _dp, _dp, _dp, vp]),
         "energy_grad_host": (i, [vp, _dp, i, _dp, _dp, _dp, _dp]),
+        "energy_grad_implicit": (i, [vp, vp, i, d, _dp, _dp, d, d, i, _dp, vp, _ip, _ip, _dp]),
         "sctm_get_env": (i, [vp, i, i, vp]),
         "sctm_workspace_high_water": (i, [vp, ctypes.POINTER(ctypes.c_size_t)]),
         "sctm_profile": (i, [vp, i, _dp]),
@@ -70,6 +71,8 @@ def load_library(path: str = LIB_PATH):
         "sctm_einsum": (i, [vp, ctypes.c_char_p, vp, _ip, vp, _ip, vp, _ip, d, d]),
         "sctm_svd_noalloc": (i, [i, i, vp, vp, vp, vp, vp]),
         "sctm_set_limits": (i, [vp, i, d]),
+        "sctm_autotune": (i, [vp, i]),
+        "sctm_autotune_table": (i, [vp, _dp, i, _ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -175,6 +178,22 @@ def energy_grad_host(h, A_cell: np.ndarray, sweeps: int, h_nn, h_diag=None, grad
     return e.value, grad_out
 
 
+def energy_grad_implicit(h, A_cell: torch.Tensor, h_nn, h_diag=None, max_sweeps: int = 300, tol: float = 0.0,
+                         fixed_point_tol: float = 0.0, solve_tol: float = 0.0, max_iter: int = 500):
+    """(E, grad, info) by implicit differentiation of the converged environment;
+    info = dict(sweeps, solver_iterations, fixed_point_change).  Zero tolerances
+    take the library defaults."""
+    a, pa = _hp(h_nn)
+    b, pb = _hp(h_diag)
+    g = torch.empty_like(A_cell)
+    e = ctypes.c_double()
+    n, it, fp = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(h, _lib.energy_grad_implicit(h, _dev(A_cell), int(max_sweeps), float(tol), pa, pb, float(fixed_point_tol),
+                                        float(solve_tol), int(max_iter), ctypes.byref(e), _dev(g), ctypes.byref(n),
+                                        ctypes.byref(it), ctypes.byref(fp)))
+    return e.value, g, {"sweeps": n.value, "solver_iterations": it.value, "fixed_point_change": fp.value}
+
+
 def sctm_get_env(h, x, y, chi, D, conventional=False, chi_I=None):
     """Environment of site (x, y): split keys (C1, T1k, T1b, ...) or, for the
     conventional algorithm, C1, T1, C2, T2, C3, T3, C4, T4 with fused edges.
@@ -266,6 +285,28 @@ def sctm_set_limits(h, svd_max_sweeps: int = 0, pipeline_wait_s: float = -1.0):
     _check(h, _lib.sctm_set_limits(h, int(svd_max_sweeps), float(pipeline_wait_s)))
 
 
+def sctm_autotune(h, enable: bool):
+    """Explore K-split counts of small-output contractions from now on (True),
+    or stop exploring (False); tuned shapes keep their choice."""
+    _check(h, _lib.sctm_autotune(h, 1 if enable else 0))
+
+
+TUNE_KERNELS = ("fp64_cuda_cores", "fp32_cuda_cores", "tf32x3_tensor_cores", "bf16_slices_tensor_cores")
+
+
+def sctm_autotune_table(h):
+    """The tuner's choices: one dict per tuned shape."""
+    n = ctypes.c_int()
+    _check(h, _lib.sctm_autotune_table(h, None, 0, ctypes.byref(n)))
+    out = np.zeros(9 * max(1, n.value))
+    _check(h, _lib.sctm_autotune_table(h, out.ctypes.data_as(_dp), n.value, ctypes.byref(n)))
+    rows = []
+    for r in out[:9 * n.value].reshape(-1, 9):
+        rows.append(dict(kernel=TUNE_KERNELS[int(r[0])], batch=int(r[1]), M=int(r[2]), N=int(r[3]), K=int(r[4]),
+                         rule_splits=int(r[5]), rule_ms=float(r[6]), chosen_splits=int(r[7]), chosen_ms=float(r[8])))
+    return rows
+
+
 def sctm_workspace_high_water(h) -> int:
     v = ctypes.c_size_t()
     _check(h, _lib.sctm_workspace_high_water(h, ctypes.byref(v)))
@@ -319,6 +360,9 @@ class SplitCTMRG:
 
     def energy_grad(self, A, sweeps, h_nn, h_diag=None):
         return energy_grad(self.h, A, sweeps, h_nn, h_diag)
+
+    def energy_grad_implicit(self, A, h_nn, h_diag=None, **kw):
+        return energy_grad_implicit(self.h, A, h_nn, h_diag, **kw)
 
     def projectors(self, direction, x, y, colour):
         # the colour that carries the physical leg: red (order 0) or yellow (order 1)

@@ -32,10 +32,20 @@ struct sctm_ctx {
     if (store) cudaFree(store);
     if (c.partial) cudaFree(c.partial);
     if (c.svd_status) cudaFree(c.svd_status);
+    for (auto& kv : c.tune) {
+      if (kv.second.e0) cudaEventDestroy(kv.second.e0);
+      if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+    }
   }
 };
 
 namespace {
+
+// an error that carries its own return code
+struct CodedError : std::runtime_error {
+  int code;
+  CodedError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
 
 int fail(sctm_handle h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -58,6 +68,9 @@ int guard(sctm_handle h, F&& f) {
   } catch (const CudaError& e) {
     rollback(h, mk);
     return fail(h, SCTM_ERR_CUDA, e.what());
+  } catch (const CodedError& e) {
+    rollback(h, mk);
+    return fail(h, e.code, e.what());
   } catch (const std::exception& e) {
     rollback(h, mk);
     std::string m = e.what();
@@ -280,7 +293,9 @@ void sweep_untaped(sctm_handle h) {
 //   Hbot^(l) = sum_{t: l_t = l} (w_t / N0) Htop(k_t) - [l = (0,0)] (E_p / N0) Htop(0,0),
 //   TL_bar(o1) += TR(o2) Htop^(o1,o2)^T,  TR_bar(o2) += TL(o1) Htop^(o1,o2),
 //   BL_bar(o3) += Hbot^(o3,o4) BR(o4),    BR_bar(o4) += Hbot^(o3,o4)^T BL(o3);
-// then the corners' tape carries the adjoints to the environment and A.
+// then the corners' tape carries the adjoints to the environment and A.  To
+// bound the memory only the Hbot are stored: each Htop is formed for its dot
+// products and dropped, and formed once more for the Hbot^ sums.
 double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed) {
   Ctx& c = h->c;
   const Params& P = h->P;
@@ -311,13 +326,19 @@ double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed
       const bool tap = c.tape.active;
       PatchCorners K = patch_corners(c, P, h->cell, ops, terms, x, y);
       c.tape.active = false;
-      std::vector<Tensor> Ht, Hb;
-      for (const Key& k : tkeys) Ht.push_back(einsum(c, "ra,rb->ab", plain(K.TL[k.first]), plain(K.TR[k.second])));
+      auto top = [&](const Key& k) { return einsum(c, "ra,rb->ab", plain(K.TL[k.first]), plain(K.TR[k.second])); };
+      const size_t mk_hb = c.arena.mark();
+      std::vector<Tensor> Hb;
       for (const Key& k : bkeys) Hb.push_back(einsum(c, "al,bl->ab", plain(K.BL[k.first]), plain(K.BR[k.second])));
+      // dot products: term i + 1, the norm N0 at 0
       std::vector<Tensor> dev(terms.size() + 1);
-      dev[0] = dot(c, Ht[0], Hb[0]);
-      for (size_t i = 0; i < terms.size(); ++i)
-        dev[i + 1] = dot(c, Ht[idx(tkeys, {terms[i].t1, terms[i].t2})], Hb[idx(bkeys, {terms[i].b1, terms[i].b2})]);
+      for (size_t ik = 0; ik < tkeys.size(); ++ik) {
+        Tensor Ht = top(tkeys[ik]);
+        if (ik == 0) dev[0] = dot(c, Ht, Hb[0]);
+        for (size_t i = 0; i < terms.size(); ++i)
+          if (Key(terms[i].t1, terms[i].t2) == tkeys[ik])
+            dev[i + 1] = dot(c, Ht, Hb[idx(bkeys, {terms[i].b1, terms[i].b2})]);
+      }
       std::vector<double> v(dev.size());
       for (size_t i = 0; i < dev.size(); ++i)
         SCTM_CUDA(cudaMemcpyAsync(&v[i], dev[i].data, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -328,11 +349,12 @@ double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed
       E += Ep;
       if (seed) {
         SCTM_CHECK(tap, "energy gradient without a tape");
-        const long long nn = Ht[0].numel();
-        // top products: Htop^(k), then the cotangents of TL(o1) and TR(o2)
+        const int n0 = Hb[0].shape[0], n1 = Hb[0].shape[1];
+        const long long nn = Hb[0].numel();
+        // top products: Htop^(k) from the stored Hbot, then the cotangents of TL(o1), TR(o2)
         for (size_t ik = 0; ik < tkeys.size(); ++ik) {
           size_t m2 = c.arena.mark();
-          Tensor Hh = c.zeros({Ht[0].shape[0], Ht[0].shape[1]});
+          Tensor Hh = c.zeros({n0, n1});
           for (size_t i = 0; i < terms.size(); ++i)
             if (Key(terms[i].t1, terms[i].t2) == tkeys[ik])
               launch_axpy(nn, terms[i].w / N0, Hb[idx(bkeys, {terms[i].b1, terms[i].b2})].data, Hh.data, c.stream);
@@ -343,18 +365,24 @@ double energy_value(sctm_handle h, const double* hn, const double* hd, bool seed
           einsum_into(c, "ra,ab->rb", plain(TL), Hh, gview(TR), 1.0, 1.0, false);
           c.arena.release(m2);
         }
-        for (size_t il = 0; il < bkeys.size(); ++il) {
+        // bottom products: the Hbot^(l) sums from each Htop formed once more
+        c.arena.release(mk_hb);   // the stored Hbot are no longer needed
+        std::vector<Tensor> Hh;
+        for (size_t il = 0; il < bkeys.size(); ++il) Hh.push_back(c.zeros({n0, n1}));
+        for (size_t ik = 0; ik < tkeys.size(); ++ik) {
           size_t m2 = c.arena.mark();
-          Tensor Hh = c.zeros({Hb[0].shape[0], Hb[0].shape[1]});
+          Tensor Ht = top(tkeys[ik]);
           for (size_t i = 0; i < terms.size(); ++i)
-            if (Key(terms[i].b1, terms[i].b2) == bkeys[il])
-              launch_axpy(nn, terms[i].w / N0, Ht[idx(tkeys, {terms[i].t1, terms[i].t2})].data, Hh.data, c.stream);
-          if (il == 0) launch_axpy(nn, -Ep / N0, Ht[0].data, Hh.data, c.stream);
+            if (Key(terms[i].t1, terms[i].t2) == tkeys[ik])
+              launch_axpy(nn, terms[i].w / N0, Ht.data, Hh[idx(bkeys, {terms[i].b1, terms[i].b2})].data, c.stream);
+          if (ik == 0) launch_axpy(nn, -Ep / N0, Ht.data, Hh[0].data, c.stream);
+          c.arena.release(m2);
+        }
+        for (size_t il = 0; il < bkeys.size(); ++il) {
           const Tensor& BL = K.BL[bkeys[il].first];
           const Tensor& BR = K.BR[bkeys[il].second];
-          einsum_into(c, "ab,bl->al", Hh, plain(BR), gview(BL), 1.0, 1.0, false);
-          einsum_into(c, "ab,al->bl", Hh, plain(BL), gview(BR), 1.0, 1.0, false);
-          c.arena.release(m2);
+          einsum_into(c, "ab,bl->al", Hh[il], plain(BR), gview(BL), 1.0, 1.0, false);
+          einsum_into(c, "ab,al->bl", Hh[il], plain(BL), gview(BR), 1.0, 1.0, false);
         }
         c.tape.active = tap;
         c.tape.backward_from(tm);
@@ -509,34 +537,43 @@ int split_ctmrg_sweeps(sctm_handle h, int n) {
   });
 }
 
+namespace {
+// Full steps until the largest change of a normalised corner spectrum (L2 over
+// its chi values, max over corners and sites) falls below tol (Sec. II.B:
+// steps are iterated until the environment converges).
+void run_to_tol(sctm_handle h, int max_sweeps, double tol, int* sweeps_done, double* last_delta) {
+  const size_t chi = (size_t)h->P.chi;
+  std::vector<double> prev = corner_spectra(h);
+  double delta = HUGE_VAL;
+  int n = 0;
+  while (n < max_sweeps) {
+    sweep_untaped(h);
+    ++n;
+    std::vector<double> cur = corner_spectra(h);
+    delta = 0.0;
+    for (size_t c = 0; c < cur.size() / chi; ++c) {
+      double ss = 0.0;
+      for (size_t j = 0; j < chi; ++j) {
+        const double d = cur[c * chi + j] - prev[c * chi + j];
+        ss += d * d;
+      }
+      if (!std::isfinite(ss)) throw std::runtime_error("non-finite corner spectrum");
+      delta = std::max(delta, std::sqrt(ss));
+    }
+    prev.swap(cur);
+    if (delta < tol) break;
+  }
+  if (sweeps_done) *sweeps_done = n;
+  if (last_delta) *last_delta = delta;
+}
+}  // namespace
+
 int split_ctmrg_run(sctm_handle h, int max_sweeps, double tol, int* sweeps_done, double* last_delta) {
   return guard(h, [&]() {
     SCTM_CHECK(h->ready, "split_ctmrg_init must come first");
     SCTM_CHECK(max_sweeps >= 0, "max_sweeps must be >= 0");
     if (!(tol > 0)) tol = h->c.fp32_compute ? 1e-7 : 1e-12;
-    const size_t chi = (size_t)h->P.chi;
-    std::vector<double> prev = corner_spectra(h);
-    double delta = HUGE_VAL;
-    int n = 0;
-    while (n < max_sweeps) {
-      sweep_untaped(h);
-      ++n;
-      std::vector<double> cur = corner_spectra(h);
-      delta = 0.0;
-      for (size_t c = 0; c < cur.size() / chi; ++c) {
-        double ss = 0.0;
-        for (size_t j = 0; j < chi; ++j) {
-          const double d = cur[c * chi + j] - prev[c * chi + j];
-          ss += d * d;
-        }
-        if (!std::isfinite(ss)) throw std::runtime_error("non-finite corner spectrum");
-        delta = std::max(delta, std::sqrt(ss));
-      }
-      prev.swap(cur);
-      if (delta < tol) break;
-    }
-    if (sweeps_done) *sweeps_done = n;
-    if (last_delta) *last_delta = delta;
+    run_to_tol(h, max_sweeps, tol, sweeps_done, last_delta);
   });
 }
 
@@ -696,6 +733,154 @@ int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const
   return rc;
 }
 
+int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps, double tol,
+                         const double* h_nn_host, const double* h_diag_host, double fixed_point_tol,
+                         double solve_tol, int max_iter, double* e_per_site, double* grad_dev, int* sweeps_done,
+                         int* solver_iterations, double* fixed_point_change) {
+  return guard(h, [&]() {
+    SCTM_CHECK(A_cell_dev && h_nn_host && e_per_site && grad_dev, "null argument");
+    SCTM_CHECK(max_sweeps >= 0 && max_iter >= 1, "max_sweeps must be >= 0 and max_iter >= 1");
+    // defaults: FP64 as the rule's own tolerances; the mixed precisions carry
+    // FP32-level rounding in the networks, which sets the floor of the
+    // spectral change, of the step-to-step change and of the adjoint iterate
+    const bool mixed = h->c.fp32_compute;
+    if (!(tol > 0)) tol = mixed ? 1e-7 : 1e-13;
+    if (!(fixed_point_tol > 0)) fixed_point_tol = mixed ? 1e-5 : 1e-9;
+    if (!(solve_tol > 0)) solve_tol = mixed ? 1e-6 : 1e-12;
+    Ctx& c = h->c;
+    const Params& P = h->P;
+    const long long N = (long long)P.Lx * P.Ly;
+    const long long nA = N * P.p * (long long)P.D * P.D * P.D * P.D;
+    const long long nE = N * h->env_site;
+    SCTM_CUDA(cudaMemcpyAsync(h->A, A_cell_dev, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    size_t base = c.arena.mark();
+    const size_t high_base = c.arena.mark_high();
+    // 1. the fixed point env*: initial environment, then full steps to tol
+    bind_A(h, false);
+    c.tape.active = false;
+    init_env(c, P, h->cell);
+    save_env(h, h->store);
+    bind_store(h, h->store);
+    c.arena.release(base);
+    h->ready = true;
+    int n = 0;
+    run_to_tol(h, max_sweeps, tol, &n, nullptr);
+    if (sweeps_done) *sweeps_done = n;
+    // 2. one more step f(env*) from checkpoints ck[0] = env* .. ck[4] = f(env*),
+    // keeping the decompositions of its moves for the taped recomputations
+    double* ck = c.arena.alloc(nE * 5);
+    double* gE = c.arena.alloc(nE);     // dE/denv*
+    double* x = c.arena.alloc(nE);      // adjoint iterate
+    double* xn = c.arena.alloc(nE);
+    double* gbuf = c.arena.alloc(nE);
+    double* gA0 = c.arena.alloc(nA);    // dE/dA at fixed env*
+    double* red = c.arena.alloc(2 * N * NKEY + 4);
+    save_env(h, ck);
+    bind_store(h, ck);
+    const size_t top = c.arena.mark();
+    std::vector<std::vector<std::array<Tensor, 3>>> decomp(4);
+    for (int mv = 0; mv < 4; ++mv) {
+      c.decomp = Ctx::DecompCache();
+      c.decomp.mode = 1;
+      move(c, P, h->cell, mv);
+      decomp[mv] = std::move(c.decomp.entries);
+      c.decomp = Ctx::DecompCache();
+      save_env(h, ck + (mv + 1) * nE);
+      bind_store(h, ck + (mv + 1) * nE);
+      c.arena.release(top);
+    }
+    check_svd(h);
+    // element-wise fixed point: max over tensors of max|f(env*) - env*| / max|env*|
+    {
+      long long i = 0;
+      for (int xx = 0; xx < P.Lx; ++xx)
+        for (int yy = 0; yy < P.Ly; ++yy)
+          for (int k = 0; k < NKEY; ++k, ++i) {
+            const Tensor a = key_view(h, ck, xx, yy, k), b = key_view(h, ck + 4 * nE, xx, yy, k);
+            launch_maxabs_pair(a.numel(), b.data, a.data, red + 2 * i, c.stream);
+          }
+      std::vector<double> hr(2 * i);
+      SCTM_CUDA(cudaMemcpyAsync(hr.data(), red, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      SCTM_CUDA(cudaStreamSynchronize(c.stream));
+      double worst = 0.0;
+      for (long long j = 0; j < i; ++j)
+        if (hr[2 * j + 1] > 0) worst = std::max(worst, hr[2 * j] / hr[2 * j + 1]);
+      if (fixed_point_change) *fixed_point_change = worst;
+      if (!(worst <= fixed_point_tol))
+        throw CodedError(SCTM_ERR_NOT_FIXED_POINT,
+                         "environment is not an element-wise fixed point (relative change " + std::to_string(worst) +
+                             "): the projector gauge is not fixed between steps");
+    }
+    // 3. energy at env*, taped: dE/denv* and dE/dA
+    bind_A(h, true);
+    SCTM_CUDA(cudaMemsetAsync(h->Agrad, 0, nA * sizeof(double), c.stream));
+    c.tape.active = true;
+    bind_leaves(h, ck);
+    *e_per_site = energy_value(h, h_nn_host, h_diag_host, true);
+    read_env_grad(h, gE);
+    c.tape.active = false;
+    c.arena.release(top);
+    SCTM_CUDA(cudaMemcpyAsync(gA0, h->Agrad, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    // out = x^T df/denv through the four moves of the step, each recomputed
+    // taped from its checkpoint (x^T df/dA accumulates into the A gradient)
+    auto vjp = [&](const double* xin, double* out) {
+      SCTM_CUDA(cudaMemcpyAsync(gbuf, xin, nE * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      for (int mv = 3; mv >= 0; --mv) {
+        c.tape.active = true;
+        bind_leaves(h, ck + mv * nE);
+        std::vector<SiteEnv> leaves = h->cell.env;
+        const size_t tm = c.tape.mark();
+        c.decomp = Ctx::DecompCache();
+        c.decomp.mode = 2;
+        c.decomp.entries = decomp[mv];
+        move(c, P, h->cell, mv);
+        SCTM_CHECK(c.decomp.next == c.decomp.entries.size(), "decomposition cache: entries left over");
+        c.decomp = Ctx::DecompCache();
+        seed_env_grad(h, gbuf);
+        c.tape.backward_from(tm);
+        h->cell.env = leaves;
+        read_env_grad(h, gbuf);
+        c.tape.active = false;
+        c.arena.release(top);
+      }
+      SCTM_CUDA(cudaMemcpyAsync(out, gbuf, nE * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    };
+    // 4. x = dE/denv* + x^T df/denv, iterated from x = dE/denv*
+    SCTM_CUDA(cudaMemcpyAsync(x, gE, nE * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    int it = 0;
+    bool converged = false;
+    while (it < max_iter && !converged) {
+      ++it;
+      vjp(x, xn);
+      launch_axpy(nE, 1.0, gE, xn, c.stream);                       // xn = dE/denv* + x^T df/denv
+      launch_axpy(nE, -1.0, xn, x, c.stream);                       // x <- x - xn (the change)
+      launch_dot(1, nE, x, x, 0, red, c.partial, c.stream);
+      launch_dot(1, nE, xn, xn, 0, red + 1, c.partial, c.stream);
+      double nd[2];
+      SCTM_CUDA(cudaMemcpyAsync(nd, red, sizeof(nd), cudaMemcpyDeviceToHost, c.stream));
+      SCTM_CUDA(cudaStreamSynchronize(c.stream));
+      if (!std::isfinite(nd[0]) || !std::isfinite(nd[1])) throw std::runtime_error("non-finite adjoint iterate");
+      std::swap(x, xn);
+      converged = std::sqrt(nd[0]) <= solve_tol * std::sqrt(nd[1]);
+    }
+    if (solver_iterations) *solver_iterations = it;
+    if (!converged) throw CodedError(SCTM_ERR_NO_CONVERGENCE, "adjoint fixed-point iteration did not converge");
+    check_svd(h);
+    // 5. grad = dE/dA + x^T df/dA
+    SCTM_CUDA(cudaMemsetAsync(h->Agrad, 0, nA * sizeof(double), c.stream));
+    vjp(x, xn);
+    launch_axpy(nA, 1.0, gA0, h->Agrad, c.stream);
+    check_svd(h);
+    SCTM_CUDA(cudaMemcpyAsync(grad_dev, h->Agrad, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    // env* stays in the store
+    bind_A(h, false);
+    bind_store(h, h->store);
+    SCTM_CUDA(cudaStreamSynchronize(c.stream));
+    c.arena.release(base);
+    c.arena.release_high(high_base);
+  });
+}
+
 int sctm_get_env(sctm_handle h, int x, int y, double* out_dev) {
   return guard(h, [&]() {
     SCTM_CHECK(out_dev, "null argument");
@@ -766,6 +951,39 @@ int sctm_profile(sctm_handle h, int enable, double* out) {
 
 int sctm_workspace_high_water(sctm_handle h, size_t* bytes) {
   return guard(h, [&]() { *bytes = h->c.arena.high_water(); });
+}
+
+int sctm_autotune(sctm_handle h, int enable) {
+  return guard(h, [&]() { h->c.autotune = enable != 0; });
+}
+
+int sctm_autotune_table(sctm_handle h, double* out, int max_rows, int* rows) {
+  return guard(h, [&]() {
+    SCTM_CHECK(rows && (max_rows <= 0 || out), "null argument");
+    SCTM_CUDA(cudaStreamSynchronize(h->c.stream));
+    int n = 0;
+    for (auto& kv : h->c.tune) {
+      Ctx::Tune& t = kv.second;
+      if (t.pending >= 0) {   // the last exploration call's timing
+        SCTM_CUDA(cudaEventElapsedTime(&t.ms[t.pending], t.e0, t.e1));
+        t.pending = -1;
+        if (t.next == (int)t.cand.size())
+          t.chosen = t.cand[std::min_element(t.ms.begin(), t.ms.end()) - t.ms.begin()];
+      }
+      if (!t.chosen) continue;
+      if (n < max_rows) {
+        double* r = out + 9 * (size_t)n;
+        for (int i = 0; i < 5; ++i) r[i] = (double)kv.first[i];
+        const int ic = (int)(std::find(t.cand.begin(), t.cand.end(), t.chosen) - t.cand.begin());
+        r[5] = t.cand[0];
+        r[6] = t.ms[0];
+        r[7] = t.chosen;
+        r[8] = t.ms[ic];
+      }
+      ++n;
+    }
+    *rows = n;
+  });
 }
 
 int sctm_set_limits(sctm_handle h, int svd_max_sweeps, double pipeline_wait_s) {

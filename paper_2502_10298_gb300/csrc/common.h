@@ -58,6 +58,16 @@ struct ContractDesc {
 // Offset of multi-index number `lin` of a group in operand X (stride array s).
 __host__ __device__ inline long long group_offset(const Group& g, const long long* s, long long lin) {
   long long off = 0;
+  if (lin >= 0 && lin <= 0xFFFFFFFFLL) {   // 32-bit divides: several times cheaper on the GPU
+    unsigned l = (unsigned)lin;
+    for (int i = g.nd - 1; i >= 0; --i) {
+      const unsigned sz = (unsigned)g.size[i];
+      const unsigned q = l / sz;
+      off += (long long)(l - q * sz) * s[i];
+      l = q;
+    }
+    return off;
+  }
   for (int i = g.nd - 1; i >= 0; --i) {
     long long sz = g.size[i];
     long long q = lin / sz;

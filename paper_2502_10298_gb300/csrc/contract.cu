@@ -142,7 +142,7 @@ void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, con
                           cudaStream_t s) {
   const long long total = d.B * d.M * d.N;
   if (total == 0) return;
-  ProfScope pf(PF_MISC, s, 0.0, 8.0 * total * (d.beta != 0 ? 3 : 2));
+  ProfScope pf(PF_MISC, s, 0.0, 8.0 * total * (d.beta != 0 ? 3 : 2), 1, "splitk_finish");
   const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, kNumSMs * 16);
   splitk_finish_kernel<<<blocks, 256, 0, s>>>(d, Wm, Wn, W, C);
   SCTM_CUDA(cudaGetLastError());
@@ -160,20 +160,29 @@ long long contract_splits(const ContractDesc& d) {
   if (sp < 2 || d.B > 65535) return 1;
   return std::min<long long>(sp, 65535);
 }
+long long contract_max_splits(const ContractDesc& d) {
+  const long long tiles = ((d.M + kCBM - 1) / kCBM) * ((d.N + kCBN - 1) / kCBN) * d.B;
+  if (tiles >= 2 * kNumSMs || d.B > 65535) return 1;
+  return std::max<long long>(1, std::min<long long>(d.K / kCBK, 65535));
+}
 }  // namespace
 
+int contract_split_rule(const ContractDesc& d) { return (int)contract_splits(d); }
+int contract_split_max(const ContractDesc& d) { return (int)contract_max_splits(d); }
+
 size_t contract_scratch_doubles(const ContractDesc& d) {
-  return contract_splits(d) > 1 ? (size_t)(d.B * d.M * d.N) + 32 : 0;
+  return contract_max_splits(d) > 1 ? (size_t)(d.B * d.M * d.N) + 32 : 0;
 }
 
 template <typename T>
 void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute,
-                     double* scratch) {
+                     double* scratch, int splits_req) {
   if (d.M == 0 || d.N == 0 || d.B == 0) return;
   constexpr int BM = kCBM, BN = kCBN, BK = kCBK, TM = 4, TN = 4;
   long long tiles = ((d.N + BN - 1) / BN) * ((d.M + BM - 1) / BM);
   SCTM_CHECK(tiles < (1LL << 31) && d.B <= 65535, "contraction too large for grid");
-  const long long splits = scratch ? contract_splits(d) : 1;
+  long long splits = scratch ? contract_splits(d) : 1;
+  if (scratch && splits_req > 0) splits = std::min<long long>(splits_req, contract_max_splits(d));
   const long long kchunk = splits > 1 ? (((d.K + splits - 1) / splits + BK - 1) / BK) * BK : d.K;
   const long long nsplit = (d.K + kchunk - 1) / kchunk;
   double* W = nullptr;
@@ -196,6 +205,92 @@ void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaSt
 }
 
 template void launch_contract<double>(const ContractDesc&, const double*, const double*, double*, cudaStream_t, bool,
-                                      double*);
+                                      double*, int);
+
+// ------------------------------------------------------------ symmetric Gram
+// G = Y^T Y (r x r) of a row-major m x r block Y (row stride ldy), FP64: only
+// the 64 x 64 tiles on and above the diagonal are formed, each CTA summing
+// one range of rows into W (zeroed) with atomics; gram_mirror_kernel then
+// writes both triangles.  The product is symmetric, so this is the full Gram
+// matrix for about (T + 1) / (2 T) of the multiply-adds (T tiles per side).
+constexpr int kGT = 64, kGK = 16;
+
+__global__ void __launch_bounds__(256) gram_upper_kernel(long long m, int r, const double* __restrict__ Y,
+                                                         long long ldy, long long rchunk, double* __restrict__ W) {
+  __shared__ double As[kGK][kGT + 1], Bs[kGK][kGT + 1];
+  const int T = (r + kGT - 1) / kGT;
+  // tile pair (ti <= tj) of the upper triangle, row by row
+  int t = blockIdx.x, ti = 0;
+  while (t >= T - ti) t -= T - ti, ++ti;
+  const int tj = ti + t;
+  const int i0 = ti * kGT, j0 = tj * kGT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  double acc[4][4] = {{0.0}};
+  const long long kb = (long long)blockIdx.y * rchunk, ke = min(m, kb + rchunk);
+  for (long long k0 = kb; k0 < ke; k0 += kGK) {
+    __syncthreads();
+    for (int idx = tid; idx < kGK * kGT; idx += 256) {
+      const int kk = idx / kGT, c = idx % kGT;
+      const long long k = k0 + kk;
+      const bool in = k < ke;
+      As[kk][c] = (in && i0 + c < r) ? Y[k * ldy + i0 + c] : 0.0;
+      Bs[kk][c] = (in && j0 + c < r) ? Y[k * ldy + j0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gi = i0 + ty + 16 * i, gj = j0 + tx + 16 * j;
+      if (gi < r && gj < r && gi <= gj) atomicAdd(&W[(long long)gi * r + gj], acc[i][j]);
+    }
+}
+
+__global__ void gram_mirror_kernel(int r, const double* __restrict__ W, double* __restrict__ G, long long ldg) {
+  const long long total = (long long)r * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    G[(long long)i * ldg + j] = i <= j ? W[(long long)i * r + j] : W[(long long)j * r + i];
+  }
+}
+
+void launch_gram(long long m, int r, const double* Y, long long ldy, double* G, long long ldg, double* W,
+                 cudaStream_t s) {
+  if (r == 0) return;
+  SCTM_CUDA(cudaMemsetAsync(W, 0, (size_t)r * r * sizeof(double), s));
+  const int T = (r + kGT - 1) / kGT;
+  const long long tiles = (long long)T * (T + 1) / 2;
+  // splits over the rows until about two CTAs per SM, at least one row block each
+  long long splits = std::max<long long>(1, std::min<long long>((2 * kNumSMs + tiles - 1) / tiles,
+                                                                (m + kGK - 1) / kGK));
+  splits = std::min<long long>(splits, 65535);
+  const long long rchunk = ((m + splits - 1) / splits + kGK - 1) / kGK * kGK;
+  splits = m > 0 ? (m + rchunk - 1) / rchunk : 1;
+  {
+    ProfScope ps(PF_CONTRACT, s, 2.0 * m * (double)r * r, 8.0 * m * r + 8.0 * r * r, 1, "gram");
+    if (m > 0) {
+      gram_upper_kernel<<<dim3((unsigned)tiles, (unsigned)splits), 256, 0, s>>>(m, r, Y, ldy, rchunk, W);
+      SCTM_CUDA(cudaGetLastError());
+    }
+  }
+  ProfScope pf(PF_MISC, s, 0.0, 16.0 * r * r, 1, "gram_mirror");
+  const unsigned blocks = (unsigned)std::min<long long>(((long long)r * r + 255) / 256, kNumSMs * 8);
+  gram_mirror_kernel<<<blocks, 256, 0, s>>>(r, W, G, ldg);
+  SCTM_CUDA(cudaGetLastError());
+}
 
 }  // namespace sctm

@@ -85,9 +85,19 @@ struct SliceKeepScope {
   }
 };
 
-// G = Y^T Y in FP64.
+// G = Y^T Y in FP64: the symmetric Gram kernel for row-major Y outside a
+// taped region (upper-triangle tiles only, rows split over extra CTAs), else
+// the general contraction.
 static Tensor gram64(Ctx& c, const Tensor& Y) {
-  // r x r output with a long row sum: the contraction splits K over extra CTAs
+  if (Y.nd == 2 && Y.stride[1] == 1 && !c.tape.active) {
+    const int r = Y.shape[1];
+    Tensor G = c.empty({r, r});
+    const size_t mk = c.arena.mark();
+    double* W = c.arena.alloc((long long)r * r);
+    launch_gram(Y.shape[0], r, Y.data, Y.stride[0], G.data, r, W, c.stream);
+    c.arena.release(mk);   // stream-ordered: later work reuses the scratch after the kernels
+    return G;
+  }
   Fp64Scope f(c);
   return einsum(c, "ai,aj->ij", Y, Y);
 }
@@ -179,7 +189,9 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
 //   y_i = (s_i^2 - P M M^T P)^-1 P (s_i u_bar_i + M v_bar_i),
 //   z_i = (s_i^2 - Q M^T M Q)^-1 Q (M^T u_bar_i + s_i v_bar_i)
 // are found by column-wise conjugate gradients (cg_steps of them), which only
-// apply M and M^T; with cg_steps = 0 every column takes the leading term below.
+// apply M and M^T; with cg_steps = 0 every column takes the first-order term
+// y_i = P (s_i u_bar_i + M v_bar_i) / s_i^2, z_i = Q (M^T u_bar_i + s_i v_bar_i) / s_i^2
+// (the expansion of the inverse to zeroth order in P M M^T P / s_i^2).
 // Then
 //   M_bar = U X V^T + Y V^T + U Z^T,
 //   X = F o (J - J^T) S + diag(S_bar) + S F o (K - K^T), J = U^T U_bar, K = V^T V_bar,
@@ -189,29 +201,20 @@ static std::vector<Trunc> randomized_svd_batch(Ctx& c, const std::vector<Tensor>
 // mixed mode), and the randomized basis leaks a little of the top spectrum
 // into P M M^T P; so the solve is used for s_i >= 1e-3 s_1 only and a column's
 // iteration stops where its operator is not safely positive definite (see
-// launch_cg_update); smaller kept values take the leading term
-// y_i = P u_bar_i / s_i, z_i = Q v_bar_i / s_i.  Columns without cotangent stay zero.
+// launch_cg_update); smaller kept values take the first-order term.  Columns
+// without cotangent stay zero.
 static constexpr double kComplementMinRel = 1e-3;
 
 static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB, const Tensor& U, const Tensor& S,
                                   const Tensor& V, double eps_l, int cg_steps) {
   AccurateScope acc(c);
   SliceKeepScope kept(c, {rhoT, rhoB});
-  // FP64 arithmetic up to M_bar's factors: the complement terms divide
-  // P U_bar by s_i, and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level
-  // rounding of it, amplified by 1/s_i up to the inverse cutoff, swamps the
-  // gradient.  The final products with rho run in the handle's precision.
-  Fp64Scope f64(c);
   const int k = S.shape[0];
   const int nb = U.shape[0];
   Tensor gU = no_grad(U), gV = no_grad(V), gS = no_grad(S);
   gU.data = U.grad;
   gV.data = V.grad;
   gS.data = S.grad;
-  Tensor J = c.empty({k, k}), K = c.empty({k, k}), X = c.empty({k, k});
-  einsum_into(c, "ai,aj->ij", U, gU, J, 1.0, 0.0, false);
-  einsum_into(c, "ai,aj->ij", V, gV, K, 1.0, 0.0, false);
-  launch_svd_adj_inner(k, S.data, J.data, K.data, gS.data, X.data, eps_l, c.stream);
   // products with M = rhoB rhoT and M^T on beta x k blocks
   auto Mx = [&](const Tensor& x) { return einsum(c, "ab,bj->aj", rhoB, einsum(c, "ab,bj->aj", rhoT, x)); };
   auto MTx = [&](const Tensor& x) { return einsum(c, "ba,bj->aj", rhoT, einsum(c, "ba,bj->aj", rhoB, x)); };
@@ -219,6 +222,29 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
     einsum_into(c, "ai,ij->aj", B, einsum(c, "ai,aj->ij", B, x), x, -1.0, 1.0, false);
     return x;
   };
+  // M Q v_bar and M^T P u_bar of the first-order coupling.  With exact
+  // singular vectors P M V = 0 and these equal P M v_bar, P M^T u_bar; the
+  // computed triplets are Ritz vectors whose residual P M V, divided by s_i^2,
+  // would swamp the term, so only the parts of the cotangents outside the
+  // computed spaces are multiplied (projections in FP64, products in the
+  // accurate form of the handle's precision: their rounding is divided by s_i^2)
+  Tensor Mv, Mu;
+  {
+    Fp64Scope f(c);
+    Mv = project(V, copy(c, gV));
+    Mu = project(U, copy(c, gU));
+  }
+  Mv = Mx(Mv);
+  Mu = MTx(Mu);
+  // FP64 arithmetic up to M_bar's factors: the complement terms divide
+  // P U_bar by s_i, and P U_bar = U_bar - U (U^T U_bar) cancels; FP32-level
+  // rounding of it, amplified by 1/s_i up to the inverse cutoff, swamps the
+  // gradient.  The final products with rho run in the handle's precision.
+  Fp64Scope f64(c);
+  Tensor J = c.empty({k, k}), K = c.empty({k, k}), X = c.empty({k, k});
+  einsum_into(c, "ai,aj->ij", U, gU, J, 1.0, 0.0, false);
+  einsum_into(c, "ai,aj->ij", V, gV, K, 1.0, 0.0, false);
+  launch_svd_adj_inner(k, S.data, J.data, K.data, gS.data, X.data, eps_l, c.stream);
   Tensor s2 = c.empty({k});
   einsum_into(c, "j,j->j", S, S, s2, 1.0, 0.0, false);   // s_j^2
   // masks: m_j = 1 for s_j >= kComplementMinRel s_1 (solved), else 0 (leading term)
@@ -254,21 +280,27 @@ static void truncated_svd_adjoint(Ctx& c, const Tensor& rhoT, const Tensor& rhoB
   Tensor bY, bZ;
   if (cg_steps > 0) {
     bY = scale_dim(c, gU, 1, S);
-    launch_axpy(bY.numel(), 1.0, Mx(gV).data, bY.data, c.stream);
+    launch_axpy(bY.numel(), 1.0, Mv.data, bY.data, c.stream);
     bY = project(U, bY);
     bZ = scale_dim(c, gV, 1, S);
-    launch_axpy(bZ.numel(), 1.0, MTx(gU).data, bZ.data, c.stream);
+    launch_axpy(bZ.numel(), 1.0, Mu.data, bZ.data, c.stream);
     bZ = project(V, bZ);
   }
   Tensor A = cg_steps > 0 ? solve(U, scale_dim(c, bY, 1, msk), true) : c.zeros({nb, k});
   Tensor Bm = cg_steps > 0 ? solve(V, scale_dim(c, bZ, 1, msk), false) : c.zeros({nb, k});
-  // leading terms for the unmasked columns: P U_bar S^-1, Q V_bar S^-1
+  // first-order terms for the unmasked columns:
+  // P (U_bar S^-1 + M V_bar S^-2), Q (V_bar S^-1 + M^T U_bar S^-2)
   {
-    Tensor w = c.empty({k});
+    Tensor w = c.empty({k}), w2 = c.empty({k});
     einsum_into(c, "j,j->j", sinv, sinv, w, 1.0, 0.0, false);   // 1/s
     einsum_into(c, "j,j->j", w, nmsk, w, 1.0, 0.0, false);
-    Tensor yl = project(U, scale_dim(c, gU, 1, w));
-    Tensor zl = project(V, scale_dim(c, gV, 1, w));
+    einsum_into(c, "j,j->j", w, w, w2, 1.0, 0.0, false);        // 1/s^2 (masked)
+    Tensor yl = scale_dim(c, gU, 1, w);
+    launch_axpy(yl.numel(), 1.0, scale_dim(c, Mv, 1, w2).data, yl.data, c.stream);
+    Tensor zl = scale_dim(c, gV, 1, w);
+    launch_axpy(zl.numel(), 1.0, scale_dim(c, Mu, 1, w2).data, zl.data, c.stream);
+    yl = project(U, yl);
+    zl = project(V, zl);
     launch_axpy(A.numel(), 1.0, yl.data, A.data, c.stream);
     launch_axpy(Bm.numel(), 1.0, zl.data, Bm.data, c.stream);
   }

@@ -9,9 +9,17 @@ namespace sctm {
 // with few 64 x 64 tiles and a long K are then split over K into an FP64
 // buffer and finished by launch_splitk_finish.
 template <typename T>
+// splits_req > 0 asks for that many K splits (clamped to contract_split_max);
+// 0 takes the rule (contract_split_rule)
 void launch_contract(const ContractDesc& d, const T* A, const T* B, T* C, cudaStream_t s, bool fp32_compute,
-                     double* scratch = nullptr);
+                     double* scratch = nullptr, int splits_req = 0);
 size_t contract_scratch_doubles(const ContractDesc& d);
+// G (r x r, row stride ldg) = Y^T Y of a row-major m x r block Y (row stride ldy), FP64;
+// W: r * r doubles of scratch
+void launch_gram(long long m, int r, const double* Y, long long ldy, double* G, long long ldg, double* W,
+                 cudaStream_t s);
+int contract_split_rule(const ContractDesc& d);
+int contract_split_max(const ContractDesc& d);
 // C = alpha W + beta C through the output strides of d; W[b][m][n] with Wm x Wn per batch
 void launch_splitk_finish(const ContractDesc& d, long long Wm, long long Wn, const double* W, double* C,
                           cudaStream_t s);
@@ -28,7 +36,9 @@ size_t tc_scratch_floats(const ContractDesc& d);
 // wait_ns: main-loop mbarrier wait limit (global time); the drain waits after a
 // timeout keep the full default limit of two seconds
 void launch_contract_tc(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
-                        float* scratch, int* status, unsigned long long wait_ns = 2000000000ull);
+                        float* scratch, int* status, unsigned long long wait_ns = 2000000000ull, int splits_req = 0);
+int tc_split_rule(const ContractDesc& d);
+int tc_split_max(const ContractDesc& d);
 
 // Tensor-core form with FP64-grade accuracy (precision 4): operands scaled per
 // row / column by powers of two and split into four BF16 digit slices, ten
@@ -49,7 +59,9 @@ SlicePanel slice_pack(const ContractDesc& d, bool b_operand, const double* X, vo
 // the same operand layout); null = pack them here into the scratch
 void launch_contract_slices(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
                             void* scratch, int* status, unsigned long long wait_ns = 2000000000ull,
-                            const SlicePanel* preA = nullptr, const SlicePanel* preB = nullptr);
+                            const SlicePanel* preA = nullptr, const SlicePanel* preB = nullptr, int splits_req = 0);
+int slice_split_rule(const ContractDesc& d);
+int slice_split_max(const ContractDesc& d);
 
 // deterministic N(0,1) test matrix (counter-based hash + Box-Muller), rows x cols
 void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s);
@@ -138,5 +150,7 @@ void launch_coldot(long long rows, int r, const double* X, const double* Y, doub
 // R, zero column of T).
 void launch_chol_qr_factor(int r, int batch, double* G, double* T, double tol_rel, cudaStream_t s);
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s);
+// out[0] = max |a - b|, out[1] = max |a| (device, two doubles)
+void launch_maxabs_pair(long long n, const double* a, const double* b, double* out, cudaStream_t s);
 
 }  // namespace sctm

@@ -34,7 +34,7 @@ template <typename T>
 void launch_copy(const Group& g, T alpha, const T* in, T beta, T* out, cudaStream_t s) {
   long long total = g.total();
   if (total == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 8.0 * total * (beta != T(0) ? 3 : 2), 1, "copy");
   copy_kernel<T><<<grid_for(total), kThreads, 0, s>>>(g, total, alpha, in, beta, out);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -55,7 +55,7 @@ void launch_scale_rc(int batch, int rows, int cols, double* X, const double* v, 
                      cudaStream_t s) {
   long long total = (long long)batch * rows * cols;
   if (total == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "scale_rc");
   scale_rc_kernel<<<grid_for(total), kThreads, 0, s>>>(batch, rows, cols, X, v, vstride, row);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -77,7 +77,7 @@ __global__ void spectrum_map_kernel(int batch, int n, int kout, const double* S,
 void launch_spectrum_map(int batch, int n, int kout, const double* S, double* w, double cutoff, int mode,
                          cudaStream_t s) {
   if (batch * kout == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "spectrum_map");
   spectrum_map_kernel<<<grid_for(batch * kout), kThreads, 0, s>>>(batch, n, kout, S, w, cutoff, mode);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -106,7 +106,7 @@ void launch_sign_find(int rows, int cols, const double* P, long long rs, long lo
                       cudaStream_t s) {
   if (rows == 0) return;
   long long threads = (long long)rows * 32;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "sign_find");
   sign_find_kernel<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, s>>>(rows, cols, P, rs, cs, sgn);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -136,7 +136,7 @@ void launch_svd_adj_inner(int n, const double* S, const double* J, const double*
                           double* inner, double eps, cudaStream_t s) {
   long long total = (long long)n * n;
   if (total == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "svd_adj_inner");
   svd_adj_inner_kernel<<<grid_for(total), kThreads, 0, s>>>(n, S, J, K, Sbar, inner, eps);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -155,7 +155,7 @@ __global__ void spectrum_adj_kernel(int n, int kout, const double* S, const doub
 void launch_spectrum_adj(int n, int kout, const double* S, const double* wbar, double* Sbar, double cutoff,
                          int mode, cudaStream_t s) {
   if (kout == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "spectrum_adj");
   spectrum_adj_kernel<<<(kout + 255) / 256, 256, 0, s>>>(n, kout, S, wbar, Sbar, cutoff, mode);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -175,7 +175,7 @@ __global__ void rescale_adj_kernel(long long n, const double* ybar, const double
 void launch_rescale_adj(long long n, const double* ybar, const double* y, const double* m, const long long* k,
                         const double* xk_sign, const double* dot, double* xbar, cudaStream_t s) {
   if (n == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "rescale_adj");
   rescale_adj_kernel<<<grid_for(n), kThreads, 0, s>>>(n, ybar, y, m, k, xk_sign, dot, xbar);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -237,7 +237,7 @@ __global__ void maxabs_final_scale_kernel(long long n, double* X, long long stri
 void launch_rescale(int batch, long long n, double* X, long long stride, double* scale, long long* argmax,
                     double* partial, cudaStream_t s) {
   if (batch == 0 || n == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 2);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 2, "rescale");
   maxabs_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, X, stride, partial);
   SCTM_CUDA(cudaGetLastError());
   maxabs_final_scale_kernel<<<batch, 1024, 0, s>>>(n, X, stride, partial, scale, argmax);
@@ -270,7 +270,7 @@ __global__ void dot_final_kernel(int batch, const double* partial, double* out) 
 void launch_dot(int batch, long long n, const double* x, const double* y, long long stride, double* out,
                 double* partial, cudaStream_t s) {
   if (batch == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 2);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 2, "dot");
   dot_partial_kernel<<<dim3(kRedBlocks, batch), kThreads, 0, s>>>(n, x, y, stride, partial);
   SCTM_CUDA(cudaGetLastError());
   dot_final_kernel<<<(batch + 127) / 128, 128, 0, s>>>(batch, partial, out);
@@ -287,13 +287,13 @@ __global__ void axpy_kernel(long long n, double a, const double* x, double* y) {
 }
 void launch_fill(long long n, double v, double* x, cudaStream_t s) {
   if (n == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "fill");
   fill_kernel<<<grid_for(n), kThreads, 0, s>>>(n, v, x);
   SCTM_CUDA(cudaGetLastError());
 }
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t s) {
   if (n == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "axpy");
   axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -318,7 +318,7 @@ __global__ void gaussian_kernel(long long n, unsigned long long seed, double* X)
 void launch_gaussian(long long rows, long long cols, unsigned long long seed, double* X, cudaStream_t s) {
   long long n = rows * cols;
   if (n == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "gaussian");
   gaussian_kernel<<<grid_for(n), kThreads, 0, s>>>(n, seed, X);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -333,7 +333,7 @@ __global__ void axpy_dev_kernel(long long n, const double* __restrict__ a, const
 
 void launch_axpy_dev(long long n, const double* a, const double* x, double* y, cudaStream_t s) {
   if (n == 0) return;
-  ProfScope ps_(PF_MISC, s, 2.0 * n, 24.0 * n);
+  ProfScope ps_(PF_MISC, s, 2.0 * n, 24.0 * n, 1, "axpy_dev");
   axpy_dev_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -357,7 +357,7 @@ void launch_scale_dim(const Group& g, int dim, const double* in, const double* v
                       cudaStream_t s) {
   const long long total = g.total();
   if (total == 0) return;
-  ProfScope ps_(PF_MISC, s, (double)total, 24.0 * total);
+  ProfScope ps_(PF_MISC, s, (double)total, 24.0 * total, 1, "scale_dim");
   scale_dim_kernel<<<grid_for(total), kThreads, 0, s>>>(g, total, dim, in, v, beta, out);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -393,7 +393,7 @@ void launch_scale_dim_reduce(const Group& g, int dim, const double* a, const dou
                              cudaStream_t s) {
   const long long total = g.total();
   if (total == 0) return;
-  ProfScope ps_(PF_MISC, s, 2.0 * total, 16.0 * total);
+  ProfScope ps_(PF_MISC, s, 2.0 * total, 16.0 * total, 1, "scale_dim_reduce");
   const long long sz = g.size[dim];
   const long long per_j = total / sz;
   const unsigned ys = (unsigned)std::max<long long>(1, std::min<long long>((per_j + kThreads - 1) / kThreads,
@@ -430,7 +430,7 @@ __global__ void coldot_kernel(long long rows, int r, const double* __restrict__ 
 
 void launch_coldot(long long rows, int r, const double* X, const double* Y, double* out, cudaStream_t s) {
   if (r == 0) return;
-  ProfScope ps_(PF_MISC, s, 2.0 * rows * r, 16.0 * rows * r);
+  ProfScope ps_(PF_MISC, s, 2.0 * rows * r, 16.0 * rows * r, 1, "coldot");
   coldot_kernel<<<(r + 31) / 32, dim3(32, 8), 0, s>>>(rows, r, X, Y, out);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -471,7 +471,7 @@ void launch_cg_update(long long rows, int r, const double* P, const double* Q, d
                       const double* rr, const double* pq, const double* pp, const double* s2, int* frozen,
                       cudaStream_t s) {
   if (rows * r == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "cg_update");
   cg_update_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, Q, Y, R, rr, pq, pp, s2, frozen);
   SCTM_CUDA(cudaGetLastError());
 }
@@ -479,8 +479,36 @@ void launch_cg_update(long long rows, int r, const double* P, const double* Q, d
 void launch_cg_direction(long long rows, int r, double* P, const double* R, const double* rr_new, const double* rr,
                          const int* frozen, cudaStream_t s) {
   if (rows * r == 0) return;
-  ProfScope ps_(PF_MISC, s, 0.0, 0.0);
+  ProfScope ps_(PF_MISC, s, 0.0, 0.0, 1, "cg_direction");
   cg_direction_kernel<<<grid_for(rows * r), kThreads, 0, s>>>(rows, r, P, R, rr_new, rr, frozen);
+  SCTM_CUDA(cudaGetLastError());
+}
+
+// out[0] = max |a - b|, out[1] = max |a| over n entries (out zeroed by the
+// caller).  The bit patterns of non-negative doubles order like the values, so
+// an integer atomicMax on them is a max of the doubles.
+__global__ void maxabs_pair_kernel(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                                   unsigned long long* out) {
+  double md = 0.0, ma = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    md = fmax(md, fabs(a[e] - b[e]));
+    ma = fmax(ma, fabs(a[e]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+    ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(md));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(ma));
+  }
+}
+
+void launch_maxabs_pair(long long n, const double* a, const double* b, double* out, cudaStream_t s) {
+  SCTM_CUDA(cudaMemsetAsync(out, 0, 2 * sizeof(double), s));
+  if (n == 0) return;
+  ProfScope ps_(PF_MISC, s, 0.0, 16.0 * n, 1, "maxabs_pair");
+  maxabs_pair_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, b, reinterpret_cast<unsigned long long*>(out));
   SCTM_CUDA(cudaGetLastError());
 }
 

@@ -209,6 +209,42 @@ static const SlicePanel* kept_slice_panel(Ctx& c, const ContractDesc& d, bool b_
   return &out;
 }
 
+// Split-K autotuner.  Contractions whose output has too few tiles to fill the
+// GPU can split K over more CTAs; the kernels choose the count by a rule.
+// With Ctx::autotune on, the first calls of each such shape (kernel, batch,
+// M, N, K) run with the rule's count, half and twice it and no split, one per
+// call -- each a complete contraction -- timed with events on the stream, and
+// later calls use the fastest.  Returns the split count to request (0: rule).
+static int tune_splits(Ctx& c, int kernel, const ContractDesc& d, int rule, int maxs, Ctx::Tune** slot) {
+  *slot = nullptr;
+  if (maxs < 2) return 0;
+  const std::vector<long long> key{kernel, d.B, d.M, d.N, d.K};
+  auto it = c.tune.find(key);
+  if (it == c.tune.end()) {
+    if (!c.autotune) return 0;
+    Ctx::Tune t;
+    for (int v : {rule, std::max(1, rule / 2), std::min(maxs, 2 * rule), 1})
+      if (std::find(t.cand.begin(), t.cand.end(), v) == t.cand.end()) t.cand.push_back(v);
+    t.ms.assign(t.cand.size(), 0.f);
+    SCTM_CUDA(cudaEventCreate(&t.e0));
+    SCTM_CUDA(cudaEventCreate(&t.e1));
+    it = c.tune.emplace(key, t).first;
+  }
+  Ctx::Tune& t = it->second;
+  if (t.pending >= 0) {   // the previous call's timing
+    SCTM_CUDA(cudaEventSynchronize(t.e1));
+    SCTM_CUDA(cudaEventElapsedTime(&t.ms[t.pending], t.e0, t.e1));
+    t.pending = -1;
+    if (t.next == (int)t.cand.size())
+      t.chosen = t.cand[std::min_element(t.ms.begin(), t.ms.end()) - t.ms.begin()];
+  }
+  if (t.chosen) return t.chosen;
+  if (!c.autotune || t.next >= (int)t.cand.size()) return 0;
+  t.pending = t.next++;
+  *slot = &t;
+  return t.cand[t.pending];
+}
+
 void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, const Tensor& C, double alpha,
                  double beta, bool record) {
   Spec sp = parse(spec);
@@ -224,6 +260,7 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
   // inside an accurate scope of the BF16-slice mode, every contraction whose
   // shape fits the tiles takes the slice kernel and the rest run in FP64
   const bool accurate = c.bf16_slices && c.accurate > 0 && c.fp32_compute;
+  Ctx::Tune* timed = nullptr;
   if (c.fp32_compute && c.tensor_cores && (accurate ? tc_shape_ok(d) : tc_eligible(d))) {
     size_t mk = c.arena.mark();
     if (c.bf16_slices) {
@@ -231,19 +268,28 @@ void einsum_into(Ctx& c, const char* spec, const Tensor& A, const Tensor& B, con
       const SlicePanel* ppa = kept_slice_panel(c, d, false, A.data, pa);
       const SlicePanel* ppb = kept_slice_panel(c, d, true, B.data, pb);
       void* scratch = c.arena.alloc((long long)(slice_scratch_bytes(d) + 7) / 8);
-      launch_contract_slices(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns, ppa, ppb);
+      const int sp = tune_splits(c, 3, d, slice_split_rule(d), slice_split_max(d), &timed);
+      if (timed) SCTM_CUDA(cudaEventRecord(timed->e0, c.stream));
+      launch_contract_slices(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns, ppa, ppb,
+                             sp);
     } else {
       float* scratch = reinterpret_cast<float*>(c.arena.alloc((long long)(tc_scratch_floats(d) + 1) / 2));
-      launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns);
+      const int sp = tune_splits(c, 2, d, tc_split_rule(d), tc_split_max(d), &timed);
+      if (timed) SCTM_CUDA(cudaEventRecord(timed->e0, c.stream));
+      launch_contract_tc(d, A.data, B.data, C.data, c.stream, scratch, c.svd_status + 32, c.pipe_wait_ns, sp);
     }
     c.arena.release(mk);   // stream-ordered: later work on the stream reuses it after the GEMM
   } else {
     const size_t wn = contract_scratch_doubles(d);
     size_t mk = c.arena.mark();
     double* scratch = wn ? c.arena.alloc((long long)wn) : nullptr;
-    launch_contract<double>(d, A.data, B.data, C.data, c.stream, c.fp32_compute && !accurate, scratch);
+    const bool f32 = c.fp32_compute && !accurate;
+    const int sp = tune_splits(c, f32 ? 1 : 0, d, contract_split_rule(d), contract_split_max(d), &timed);
+    if (timed) SCTM_CUDA(cudaEventRecord(timed->e0, c.stream));
+    launch_contract<double>(d, A.data, B.data, C.data, c.stream, f32, scratch, sp);
     c.arena.release(mk);
   }
+  if (timed) SCTM_CUDA(cudaEventRecord(timed->e1, c.stream));
   if (prof_enabled()) prof_set_tag("");
   if (!record || !c.tape.active || !C.grad) return;
   std::string sa = sp.c + "," + sp.b + "->" + sp.a;

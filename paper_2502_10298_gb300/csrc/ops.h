@@ -3,6 +3,7 @@
 // closure that accumulates the adjoints of its inputs.
 #pragma once
 #include <array>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -38,6 +39,16 @@ struct Ctx {
   // stack), keyed by the operand's layout in the contraction.
   std::vector<const double*> slice_keep;
   std::vector<std::pair<std::vector<long long>, SlicePanel>> slice_panels;
+  // Split-K autotuner (see einsum_into): per contraction shape, the split
+  // counts tried, their device times, and the choice once all are timed.
+  struct Tune {
+    std::vector<int> cand;
+    std::vector<float> ms;
+    int next = 0, pending = -1, chosen = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+  };
+  bool autotune = false;
+  std::map<std::vector<long long>, Tune> tune;
   int svd_max_sweeps = 60;       // Jacobi sweep limit (fault-injection hook: sctm_set_limits)
   unsigned long long pipe_wait_ns = 2000000000ull;   // tensor-core main-loop wait limit (same hook)
 

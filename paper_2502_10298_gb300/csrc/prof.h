@@ -11,8 +11,8 @@ enum ProfFamily { PF_CONTRACT = 0, PF_SVD = 1, PF_MISC = 2, PF_TENSOR = 3, PF_N 
 
 void prof_enable(bool on);
 // label attached to the scopes opened until the next call (e.g. an einsum
-// spec with its dimensions); with SCTM_PROFILE_TAGS set in the environment,
-// prof_collect also prints the 40 labels with the most device time to stderr
+// spec with its dimensions); with SCTM_PROFILE_TAGS=<rows> in the environment,
+// prof_collect also prints the labels with the most device time to stderr
 void prof_set_tag(const char* tag);
 bool prof_enabled();
 // out: PF_N rows of {milliseconds, launches, flops, bytes}
@@ -27,8 +27,9 @@ struct ProfTag {
 };
 
 struct ProfScope {
-  // launches: kernel launches inside the scope
-  ProfScope(int family, cudaStream_t s, double flops, double bytes, int launches = 1);
+  // launches: kernel launches inside the scope; name: the kernel, appended to
+  // the current label in the tagged summary
+  ProfScope(int family, cudaStream_t s, double flops, double bytes, int launches = 1, const char* name = nullptr);
   ~ProfScope();
   int fam;
   cudaStream_t st;

@@ -353,7 +353,7 @@ bool tc_eligible(const ContractDesc& d) {
 
 // K splits: only when the output has too few tiles to fill the GPU; at least
 // 4 slabs (128 of K) per split
-static int tc_splits(const ContractDesc& d) {
+int tc_split_rule(const ContractDesc& d) {
   const long long tiles = (round_up(d.M, TC_BM) / TC_BM) * (round_up(d.N, TC_BN) / TC_BN) * d.B;
   const long long nk = round_up(d.K, TC_BK) / TC_BK;
   const long long want = (2 * kNumSMs + tiles - 1) / tiles;
@@ -363,15 +363,23 @@ static int tc_splits(const ContractDesc& d) {
   return (int)((nk + per - 1) / per);
 }
 
+// largest split count worth trying: outputs with too few tiles to fill the
+// GPU, at least 4 slabs (128 of K) per split
+int tc_split_max(const ContractDesc& d) {
+  const long long tiles = (round_up(d.M, TC_BM) / TC_BM) * (round_up(d.N, TC_BN) / TC_BN) * d.B;
+  if (tiles >= 2 * kNumSMs) return 1;
+  return (int)std::max<long long>(1, std::min<long long>(65535, round_up(d.K, TC_BK) / TC_BK / 4));
+}
+
 size_t tc_scratch_floats(const ContractDesc& d) {
   const long long Kp = round_up(d.K, TC_BK), Mp = round_up(d.M, TC_BM), Np = round_up(d.N, TC_BN);
   size_t f = (size_t)2 * d.B * Kp * (Mp + Np) + 64;
-  if (tc_splits(d) > 1) f += (size_t)2 * d.B * Mp * Np + 64;   // FP64 partial sums
+  if (tc_split_max(d) > 1) f += (size_t)2 * d.B * Mp * Np + 64;   // FP64 partial sums
   return f;
 }
 
 void launch_contract_tc(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
-                        float* scratch, int* status, unsigned long long wait_ns) {
+                        float* scratch, int* status, unsigned long long wait_ns, int splits_req) {
   if (d.M == 0 || d.N == 0 || d.B == 0) return;
   const long long Kp = round_up(d.K, TC_BK), Mp = round_up(d.M, TC_BM), Np = round_up(d.N, TC_BN);
   float* pa = scratch;
@@ -392,12 +400,12 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
   pB.nb = d.B, pB.R = d.N, pB.K = d.K, pB.Rp = Np, pB.Kp = Kp, pB.k_inner = d.b_n_inner ? 0 : 1;
   // packing is a gather: reads the FP64 operand once, writes its hi and lo panels
   {
-    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.M * d.K + 8.0 * d.B * Kp * Mp);
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.M * d.K + 8.0 * d.B * Kp * Mp, 1, "tf32_pack");
     pack_tf32x2_kernel<<<dim3((unsigned)((Kp / 32) * (Mp / 32)), (unsigned)d.B), dim3(32, 8), 0, s>>>(pA, A, pa);
     SCTM_CUDA(cudaGetLastError());
   }
   {
-    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.N * d.K + 8.0 * d.B * Kp * Np);
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * d.B * d.N * d.K + 8.0 * d.B * Kp * Np, 1, "tf32_pack");
     pack_tf32x2_kernel<<<dim3((unsigned)((Kp / 32) * (Np / 32)), (unsigned)d.B), dim3(32, 8), 0, s>>>(pB, B, pb);
     SCTM_CUDA(cudaGetLastError());
   }
@@ -413,8 +421,10 @@ void launch_contract_tc(const ContractDesc& d, const double* A, const double* B,
     attr = true;
   }
   const int nk = (int)(Kp / TC_BK);
-  const int splits = tc_splits(d);
+  int splits = tc_split_rule(d);
+  if (splits_req > 0) splits = std::min(splits_req, tc_split_max(d));
   const int per = (nk + splits - 1) / splits;
+  splits = (nk + per - 1) / per;
   double* W = nullptr;
   if (splits > 1) {
     W = reinterpret_cast<double*>(pb + 2 * d.B * Np * Kp + 32);   // 128-byte aligned (offsets are multiples of 32 floats)

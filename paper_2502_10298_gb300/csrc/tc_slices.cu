@@ -110,29 +110,6 @@ struct SlicePack {
   int k_inner;                 // 1 when the operand is contiguous along k
 };
 
-// 32 x 32 tile of the operand, gathered so that both the strided read and the
-// shared-memory write are coalesced; zero outside the operand.
-__device__ __forceinline__ void gather_tile(const SlicePack& p, const double* __restrict__ X, long long r0,
-                                            long long k0, long long b, double (*tile)[33], long long* offR,
-                                            long long* offK) {
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  if (tid < 32) {
-    long long r = r0 + tid;
-    offR[tid] = r < p.R ? group_offset(p.rows, p.rows.sa, r) : -1;
-  } else if (tid < 64) {
-    long long k = k0 + tid - 32;
-    offK[tid - 32] = k < p.K ? group_offset(p.k, p.k.sa, k) : -1;
-  }
-  const long long ob = group_offset(p.bat, p.bat.sa, b);
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    int rr = p.k_inner ? i : tx, kk = p.k_inner ? tx : i;
-    long long orr = offR[rr], ok = offK[kk];
-    tile[rr][kk] = (orr >= 0 && ok >= 0) ? X[ob + orr + ok] : 0.0;
-  }
-  __syncthreads();
-}
-
 // Binary exponent e with |v| < 2^e (the exponent field minus 1022; subnormals
 // take -1022), or kNoExp for v = 0: integer work on the bits only, since every
 // FP64 instruction is expensive on this GPU.
@@ -143,20 +120,119 @@ __device__ __forceinline__ int exponent_bound(double v) {
   return E == 0 ? -1022 : E - 1022;
 }
 
+// Pack kernels: 256 threads per CTA, a tile of 32 rows x TK values of k
+// gathered through the operand's strides into shared memory (both the strided
+// read and the shared-memory write coalesced), then read back by row in chunks
+// of 8 consecutive k, so that every slice is written with 16-byte stores.
+constexpr int SP_ROWS = 32;
+constexpr int SP_THREADS = 256;
+
+template <int TK>
+__device__ __forceinline__ void gather_tile(const SlicePack& p, const double* __restrict__ X, long long r0,
+                                            long long k0, long long b, double (*tile)[TK + 1], long long* offR,
+                                            long long* offK) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < SP_ROWS) {
+    const long long r = r0 + tid;
+    offR[tid] = r < p.R ? group_offset(p.rows, p.rows.sa, r) : -1;
+  } else if (tid < SP_ROWS + TK) {
+    const long long k = k0 + tid - SP_ROWS;
+    offK[tid - SP_ROWS] = k < p.K ? group_offset(p.k, p.k.sa, k) : -1;
+  }
+  const long long ob = group_offset(p.bat, p.bat.sa, b);
+  __syncthreads();
+  if (p.k_inner) {   // a warp reads along k within one row
+#pragma unroll
+    for (int i = warp; i < SP_ROWS; i += SP_THREADS / 32) {
+      const long long orr = offR[i];
+#pragma unroll
+      for (int j = lane; j < TK; j += 32) {
+        const long long ok = offK[j];
+        tile[i][j] = (orr >= 0 && ok >= 0) ? X[ob + orr + ok] : 0.0;
+      }
+    }
+  } else {           // a warp reads along the rows for one k
+    const long long orr = offR[lane];
+#pragma unroll 4
+    for (int j = warp; j < TK; j += SP_THREADS / 32) {
+      const long long ok = offK[j];
+      tile[lane][j] = (orr >= 0 && ok >= 0) ? X[ob + orr + ok] : 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+// Largest exponent_bound over 8 consecutive values of one tile row.
+template <int TK>
+__device__ __forceinline__ int chunk_exponent(const double (*tile)[TK + 1], int row, int kc) {
+  int e = kNoExp;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) e = max(e, exponent_bound(tile[row][kc + j]));
+  return e;
+}
+
+// Four balanced base-256 digits of v / 2^e (see slice_pack_kernel), each as
+// the raw bits of its BF16 slice value d_i 2^(-8(i-1)).
+__device__ __forceinline__ void slice_digits(double v, int e, uint16_t* d) {
+  const long long bits = __double_as_longlong(v);
+  long long Xv = 0;
+  if (e != kNoExp && (bits & 0x7FFFFFFFFFFFFFFFLL) != 0) {
+    const int E = (int)((bits >> 52) & 0x7FF);
+    const long long mant = (bits & ((1LL << 52) - 1)) | (E != 0 ? (1LL << 52) : 0);
+    const int lsb = (E == 0 ? 1 : E) - 1075;        // v = mant 2^lsb
+    const int sh = e - 38 - lsb;                     // X = round(mant / 2^sh), sh >= 14
+    const long long mag = sh >= 64 ? 0 : (((mant >> (sh - 1)) + 1) >> 1);
+    Xv = bits < 0 ? -mag : mag;
+  }
+  const long long d1 = (Xv + (1LL << 30)) >> 31;
+  long long r = Xv - (d1 << 31);
+  const long long d2 = (r + (1LL << 22)) >> 23;
+  r -= d2 << 23;
+  const long long d3 = (r + (1LL << 14)) >> 15;
+  r -= d3 << 15;
+  const long long d4 = (r + (1LL << 6)) >> 7;
+  d[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1));
+  d[1] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d2 * 0x1p-8f));
+  d[2] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d3 * 0x1p-16f));
+  d[3] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d4 * 0x1p-24f));
+}
+
+// The four slices of 8 consecutive values of one row, stored as one 16-byte
+// word per slice at panel[slice][b][r][k .. k+7].
+template <int TK>
+__device__ __forceinline__ void pack_chunk(const SlicePack& p, const double (*tile)[TK + 1], int row, int kc, int e,
+                                           long long o, uint16_t* __restrict__ out) {
+  const long long plane = p.nb * p.Rp * p.Kp;
+  uint32_t w[4][4];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    uint16_t a[4], c[4];
+    slice_digits(tile[row][kc + j], e, a);
+    slice_digits(tile[row][kc + j + 1], e, c);
+#pragma unroll
+    for (int s = 0; s < SL_NS; ++s) w[s][j / 2] = (uint32_t)a[s] | ((uint32_t)c[s] << 16);
+  }
+#pragma unroll
+  for (int s = 0; s < SL_NS; ++s)
+    *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
+
 // expo[b][r] = max over k of exponent_bound(X[b, r, k]): the smallest e with
 // |X[b, r, k]| < 2^e for every k; kNoExp (the initial value) for a zero row.
-__global__ void __launch_bounds__(256) slice_exponent_kernel(SlicePack p, const double* __restrict__ X,
-                                                            int* __restrict__ expo) {
-  __shared__ long long offR[32], offK[32];
-  __shared__ double tile[32][33];
-  const long long nkt = p.Kp / 32, t = blockIdx.x;
-  const long long k0 = (t % nkt) * 32, r0 = (t / nkt) * 32, b = blockIdx.y;
-  gather_tile(p, X, r0, k0, b, tile, offR, offK);
-  // warp ty reduces rows ty, ty + 8, ...: lane tx holds column tx
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int e = __reduce_max_sync(0xffffffffu, exponent_bound(tile[i][threadIdx.x]));
-    if (threadIdx.x == 0 && e != kNoExp && r0 + i < p.R) atomicMax(&expo[b * p.Rp + r0 + i], e);
-  }
+// Tiles of 32 rows x 64 k; a row's 8 chunks sit on 8 neighbouring lanes.
+__global__ void __launch_bounds__(SP_THREADS) slice_exponent_kernel(SlicePack p, const double* __restrict__ X,
+                                                                   int* __restrict__ expo) {
+  constexpr int TK = 64;
+  __shared__ long long offR[SP_ROWS], offK[TK];
+  __shared__ double tile[SP_ROWS][TK + 1];
+  const long long nkt = (p.Kp + TK - 1) / TK, t = blockIdx.x;
+  const long long k0 = (t % nkt) * TK, r0 = (t / nkt) * SP_ROWS, b = blockIdx.y;
+  gather_tile<TK>(p, X, r0, k0, b, tile, offR, offK);
+  const int row = threadIdx.x >> 3, kc = (threadIdx.x & 7) * 8;
+  int e = chunk_exponent<TK>(tile, row, kc);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 7) == 0 && e != kNoExp && r0 + row < p.R) atomicMax(&expo[b * p.Rp + r0 + row], e);
 }
 
 // Four BF16 slices per value: panel[slice][b][r][k] (as raw 16-bit words).
@@ -165,38 +241,41 @@ __global__ void __launch_bounds__(256) slice_exponent_kernel(SlicePack p, const 
 // d1 = round(X / 2^31), d2 = round(r1 / 2^23), d3, d4 (each |d| <= 128) come
 // from arithmetic shifts of the remainders: x = 2^-7 (d1 + 2^-8 d2 + 2^-16 d3
 // + 2^-24 d4) + r with |r| <= 2^-32.  Integer arithmetic only.
-__global__ void __launch_bounds__(256) slice_pack_kernel(SlicePack p, const double* __restrict__ X,
-                                                        const int* __restrict__ expo, uint16_t* __restrict__ out) {
-  __shared__ long long offR[32], offK[32];
-  __shared__ double tile[32][33];
-  const long long nkt = p.Kp / 32, t = blockIdx.x;
-  const long long k0 = (t % nkt) * 32, r0 = (t / nkt) * 32, b = blockIdx.y;
-  gather_tile(p, X, r0, k0, b, tile, offR, offK);
-  const long long plane = p.nb * p.Rp * p.Kp;
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int e = expo[b * p.Rp + r0 + i];
-    const long long bits = __double_as_longlong(tile[i][threadIdx.x]);
-    long long Xv = 0;
-    if (e != kNoExp && (bits & 0x7FFFFFFFFFFFFFFFLL) != 0) {
-      const int E = (int)((bits >> 52) & 0x7FF);
-      const long long mant = (bits & ((1LL << 52) - 1)) | (E != 0 ? (1LL << 52) : 0);
-      const int lsb = (E == 0 ? 1 : E) - 1075;        // v = mant 2^lsb
-      const int sh = e - 38 - lsb;                     // X = round(mant / 2^sh), sh >= 14
-      const long long mag = sh >= 64 ? 0 : (((mant >> (sh - 1)) + 1) >> 1);
-      Xv = bits < 0 ? -mag : mag;
-    }
-    const long long d1 = (Xv + (1LL << 30)) >> 31;
-    long long r = Xv - (d1 << 31);
-    const long long d2 = (r + (1LL << 22)) >> 23;
-    r -= d2 << 23;
-    const long long d3 = (r + (1LL << 14)) >> 15;
-    r -= d3 << 15;
-    const long long d4 = (r + (1LL << 6)) >> 7;
-    const long long o = (b * p.Rp + r0 + i) * p.Kp + k0 + threadIdx.x;
-    out[o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1));
-    out[plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d2 * 0x1p-8f));
-    out[2 * plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d3 * 0x1p-16f));
-    out[3 * plane + o] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d4 * 0x1p-24f));
+__global__ void __launch_bounds__(SP_THREADS) slice_pack_kernel(SlicePack p, const double* __restrict__ X,
+                                                               const int* __restrict__ expo,
+                                                               uint16_t* __restrict__ out) {
+  constexpr int TK = 64;
+  __shared__ long long offR[SP_ROWS], offK[TK];
+  __shared__ double tile[SP_ROWS][TK + 1];
+  const long long nkt = (p.Kp + TK - 1) / TK, t = blockIdx.x;
+  const long long k0 = (t % nkt) * TK, r0 = (t / nkt) * SP_ROWS, b = blockIdx.y;
+  gather_tile<TK>(p, X, r0, k0, b, tile, offR, offK);
+  const int row = threadIdx.x >> 3, kc = (threadIdx.x & 7) * 8;
+  if (k0 + kc >= p.Kp) return;                      // past the padded row (Kp is a multiple of 32)
+  const int e = expo[b * p.Rp + r0 + row];
+  pack_chunk<TK>(p, tile, row, kc, e, (b * p.Rp + r0 + row) * p.Kp + k0 + kc, out);
+}
+
+// Operands with Kp <= 128: one tile holds whole rows, so the exponents and the
+// slices come from one read of the operand.  A row's 16 chunks sit on the 16
+// lanes of a half warp; each thread takes rows r and r + 16.
+__global__ void __launch_bounds__(SP_THREADS) slice_pack_rows_kernel(SlicePack p, const double* __restrict__ X,
+                                                                    int* __restrict__ expo,
+                                                                    uint16_t* __restrict__ out) {
+  constexpr int TK = 128;
+  __shared__ long long offR[SP_ROWS], offK[TK];
+  __shared__ double tile[SP_ROWS][TK + 1];
+  const long long r0 = (long long)blockIdx.x * SP_ROWS, b = blockIdx.y;
+  gather_tile<TK>(p, X, r0, 0, b, tile, offR, offK);
+  const int kc = (threadIdx.x & 15) * 8;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int row = (threadIdx.x >> 4) + 16 * half;
+    int e = kc < p.Kp ? chunk_exponent<TK>(tile, row, kc) : kNoExp;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 15) == 0) expo[b * p.Rp + r0 + row] = e;
+    if (kc < p.Kp) pack_chunk<TK>(p, tile, row, kc, e, (b * p.Rp + r0 + row) * p.Kp + kc, out);
   }
 }
 
@@ -444,9 +523,11 @@ CUtensorMap slice_map(uint16_t* base, long long nb, long long rows, long long Kp
   return m;
 }
 
+}  // namespace
+
 // K splits: only when the output has too few tiles to fill the GPU; at least
 // one window (512 of K) per split
-int slice_splits(const ContractDesc& d) {
+int slice_split_rule(const ContractDesc& d) {
   const long long tiles = (round_up(d.M, SL_BM) / SL_BM) * (round_up(d.N, SL_BN) / SL_BN) * d.B;
   const long long nk = round_up(d.K, SL_BK) / SL_BK;
   const long long want = (2 * kNumSMs + tiles - 1) / tiles;
@@ -456,10 +537,24 @@ int slice_splits(const ContractDesc& d) {
   return (int)((nk + per - 1) / per);
 }
 
+// largest split count worth trying: outputs with too few tiles to fill the
+// GPU, at least 4 slabs (128 of K) per split
+int slice_split_max(const ContractDesc& d) {
+  const long long tiles = (round_up(d.M, SL_BM) / SL_BM) * (round_up(d.N, SL_BN) / SL_BN) * d.B;
+  if (tiles >= 2 * kNumSMs) return 1;
+  return (int)std::max<long long>(1, std::min<long long>(65535, round_up(d.K, SL_BK) / SL_BK / 4));
+}
+
+namespace {
+
 struct SliceLayout {
   long long Kp, Mp, Np;
-  size_t panelA, panelB, expA, expB, W, total;   // byte offsets
+  size_t panelA, panelB, W, total;   // byte offsets; each packed operand holds its panel and exponents
 };
+
+size_t slice_panel_bytes_of(long long nb, long long Rp, long long Kp) {
+  return (size_t)round_up((long long)SL_NS * nb * Rp * Kp * 2, 256) + (size_t)nb * Rp * 4 + 256;
+}
 
 SliceLayout slice_layout(const ContractDesc& d) {
   SliceLayout L;
@@ -470,11 +565,9 @@ SliceLayout slice_layout(const ContractDesc& d) {
     o = (size_t)round_up((long long)(o + bytes), 256);
     return at;
   };
-  L.panelA = take((size_t)SL_NS * d.B * L.Mp * L.Kp * 2);
-  L.panelB = take((size_t)SL_NS * d.B * L.Np * L.Kp * 2);
-  L.expA = take((size_t)d.B * L.Mp * 4);
-  L.expB = take((size_t)d.B * L.Np * 4);
-  L.W = slice_splits(d) > 1 ? take((size_t)d.B * L.Mp * L.Np * 8) : 0;
+  L.panelA = take(slice_panel_bytes_of(d.B, L.Mp, L.Kp));
+  L.panelB = take(slice_panel_bytes_of(d.B, L.Np, L.Kp));
+  L.W = slice_split_max(d) > 1 ? take((size_t)d.B * L.Mp * L.Np * 8) : 0;
   L.total = o;
   return L;
 }
@@ -505,7 +598,7 @@ SlicePack operand_pack(const ContractDesc& d, bool b_operand) {
 
 size_t slice_panel_bytes(const ContractDesc& d, bool b_operand) {
   const SlicePack p = operand_pack(d, b_operand);
-  return (size_t)round_up((long long)SL_NS * p.nb * p.Rp * p.Kp * 2, 256) + (size_t)p.nb * p.Rp * 4 + 256;
+  return slice_panel_bytes_of(p.nb, p.Rp, p.Kp);
 }
 
 SlicePanel slice_pack(const ContractDesc& d, bool b_operand, const double* X, void* dst, cudaStream_t s) {
@@ -514,17 +607,25 @@ SlicePanel slice_pack(const ContractDesc& d, bool b_operand, const double* X, vo
   SlicePanel out;
   out.panel = reinterpret_cast<uint16_t*>(base);
   out.expo = reinterpret_cast<int*>(base + round_up((long long)SL_NS * p.nb * p.Rp * p.Kp * 2, 256));
-  // exponents (one gather), then the slices (another); the panel is written once
   SCTM_CUDA(cudaMemsetAsync(out.expo, 0x80, (size_t)p.nb * p.Rp * 4, s));
-  const dim3 g((unsigned)((p.Kp / 32) * (p.Rp / 32)), (unsigned)p.nb);
+  if (p.Kp <= 128) {
+    // whole rows in one tile: exponents and slices from one read
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K + 2.0 * SL_NS * p.nb * p.Kp * p.Rp, 1, "slice_pack_rows");
+    slice_pack_rows_kernel<<<dim3((unsigned)(p.Rp / SP_ROWS), (unsigned)p.nb), SP_THREADS, 0, s>>>(p, X, out.expo,
+                                                                                                   out.panel);
+    SCTM_CUDA(cudaGetLastError());
+    return out;
+  }
+  // exponents (one gather), then the slices (another); the panel is written once
+  const dim3 g((unsigned)(((p.Kp + 63) / 64) * (p.Rp / SP_ROWS)), (unsigned)p.nb);
   {
-    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K);
-    slice_exponent_kernel<<<g, dim3(32, 8), 0, s>>>(p, X, out.expo);
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K, 1, "slice_exponent");
+    slice_exponent_kernel<<<g, SP_THREADS, 0, s>>>(p, X, out.expo);
     SCTM_CUDA(cudaGetLastError());
   }
   {
-    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K + 2.0 * SL_NS * p.nb * p.Kp * p.Rp);
-    slice_pack_kernel<<<g, dim3(32, 8), 0, s>>>(p, X, out.expo, out.panel);
+    ProfScope ps(PF_MISC, s, 0.0, 8.0 * p.nb * p.R * p.K + 2.0 * SL_NS * p.nb * p.Kp * p.Rp, 1, "slice_pack");
+    slice_pack_kernel<<<g, SP_THREADS, 0, s>>>(p, X, out.expo, out.panel);
     SCTM_CUDA(cudaGetLastError());
   }
   return out;
@@ -532,7 +633,7 @@ SlicePanel slice_pack(const ContractDesc& d, bool b_operand, const double* X, vo
 
 void launch_contract_slices(const ContractDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
                             void* scratch, int* status, unsigned long long wait_ns, const SlicePanel* preA,
-                            const SlicePanel* preB) {
+                            const SlicePanel* preB, int splits_req) {
   if (d.M == 0 || d.N == 0 || d.B == 0) return;
   SCTM_CHECK(tc_shape_ok(d), "contraction shape not representable on the tensor cores");
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(scratch) + 255) & ~uintptr_t(255));
@@ -551,8 +652,10 @@ void launch_contract_slices(const ContractDesc& d, const double* A, const double
     attr = true;
   }
   const int nk = (int)(L.Kp / SL_BK);
-  const int splits = slice_splits(d);
+  int splits = slice_split_rule(d);
+  if (splits_req > 0) splits = std::min(splits_req, slice_split_max(d));
   const int per = (nk + splits - 1) / splits;
+  splits = (nk + per - 1) / per;
   double* W = nullptr;
   if (splits > 1) {
     W = reinterpret_cast<double*>(base + L.W);

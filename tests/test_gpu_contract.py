@@ -47,6 +47,8 @@ CASES = [
     ("aub,bvc->auvc", (130, 6, 140), (140, 5, 150)),  # grouped m (a,u) and n (v,c)
     ("xkmy,ynk->mxn", (9, 33, 70, 11), (11, 200, 33)),  # two k dims in reversed order
     ("ai,aj->ij", (432, 108), (432, 108)),        # Gram of a tall basis: few tiles, K split 27 ways
+    ("mk,kn->mn", (1500, 128), (128, 700)),       # K = 128: whole rows in one pack tile
+    ("km,nk->mn", (128, 1500), (700, 128)),       # the same with A m-contiguous, B k-contiguous
 ]
 
 
@@ -152,14 +154,17 @@ def test_full_size_corner_product_sampled(handles):
     assert np.sqrt(np.mean(err ** 2)) <= 1e-6 * np.sqrt(np.mean(ref ** 2))
 
 
-def test_slices_exact_on_small_integers(handles):
+@pytest.mark.parametrize("K", [2000, 128])
+def test_slices_exact_on_small_integers(handles, K):
     """Integer operands |v| <= 127 are their own leading digit: every level sum
     is an exact integer below 2^24 in each 512-wide K window, and the windows
     are added without rounding, so the product must equal the FP64 one exactly
-    (K = 2000 spans four windows; 300 x 260 spans ragged tiles)."""
+    (K = 2000 spans four windows and the two-pass packing; K = 128 packs whole
+    rows in one pass; 600 x 700 spans ragged tiles)."""
     rng = np.random.default_rng(5)
-    A = rng.integers(-127, 128, (300, 2000)).astype(np.float64)
-    B = rng.integers(-127, 128, (2000, 260)).astype(np.float64)
+    A = rng.integers(-127, 128, (600, K)).astype(np.float64)
+    B = rng.integers(-127, 128, (K, 700)).astype(np.float64)
+    assert _on_tensor_cores("mk,kn->mn", A, B)
     C = S.sctm_einsum(handles[4], "mk,kn->mn", torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda"))
     assert np.array_equal(C.cpu().numpy(), A @ B)
 

@@ -168,3 +168,25 @@ def test_lbfgs_lowers_the_energy():
     assert len(trace) >= 8
     assert best < e0 - 0.1, (e0, best)
     assert best > -1.5
+
+
+def test_autotune_changes_only_the_summation_order():
+    """The split-K autotuner explores its candidates on real calls (each a
+    complete contraction) and then keeps the fastest: the energy and gradient
+    of a tuned handle equal those of an untuned one up to the summation order
+    (FP64, 2x2, D=2, chi=8), and the table lists the tuned shapes."""
+    import paper_2502_10298_gb300 as S
+    A = torch.tensor(I.random_cell(2, 2, 2, 2, seed=6), device="cuda")
+    h = I.heisenberg_bond()
+    with S.SplitCTMRG(2, 2, 2, 2, 8) as ref:
+        e0, g0 = ref.energy_grad(A, 2, h, None)
+    with S.SplitCTMRG(2, 2, 2, 2, 8) as s:
+        S.sctm_autotune(s.h, True)
+        for _ in range(5):
+            s.energy_grad(A, 2, h, None)
+        S.sctm_autotune(s.h, False)
+        e1, g1 = s.energy_grad(A, 2, h, None)
+        table = S.sctm_autotune_table(s.h)
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert float((g1 - g0).norm() / g0.norm()) <= 1e-11
+    assert table and all(r["chosen_splits"] >= 1 and r["chosen_ms"] >= 0 for r in table)

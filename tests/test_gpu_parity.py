@@ -185,7 +185,7 @@ def test_neel_and_ising_exact(S):
         assert abs(s.energy(H, 0.5 * H) - (-0.5 + 0.25)) < 1e-12
 
 
-@pytest.mark.parametrize("m,n", [(7, 7), (40, 40), (100, 60), (300, 256)])
+@pytest.mark.parametrize("m,n", [(7, 7), (40, 40), (100, 60), (300, 256), (700, 200), (3000, 300)])
 def test_jacobi_svd_against_lapack(S, m, n):
     """Singular values to 1e-13 relative; U S V^T reproduces M; U, V orthonormal."""
     rng = np.random.default_rng(m + n)
