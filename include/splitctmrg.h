@@ -64,7 +64,8 @@ typedef struct {
                                accumulation), small ones in FP32 on the CUDA cores;
                                projectors from a randomized subspace iteration (chi +
                                rank_extra columns, Cholesky-QR bases, power_steps steps)
-                               when the truncated space exceeds that and randomized_min;
+                               when the truncated space is at least four times that and
+                               at least randomized_min;
                                decompositions and Gram matrices in FP64; default
                                cutoff 1e-5.
                             2: as 1 with every contraction on the CUDA cores (FP32).

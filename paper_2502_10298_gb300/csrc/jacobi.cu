@@ -175,17 +175,18 @@ svd_kernel(int m, int n, const double* __restrict__ M, double* __restrict__ U, d
 // sweeps is bounded (max_sweeps), so the kernel always terminates.
 constexpr int kCoopThreads = 256;
 
-// Cooperative prologue shared by the multi-CTA kernels: W (column-major) = M,
-// V = I, and the noise level noise_rel ||M||_F^2 of every matrix in
-// ((double*)(flags + 64))[b]; flags zeroed.
-__device__ void coop_prologue(cg::grid_group& grid, int m, int n, int batch, const double* __restrict__ M,
-                              double* __restrict__ work, int* __restrict__ flags, double noise_rel) {
+__global__ void __launch_bounds__(kCoopThreads)
+svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* __restrict__ U,
+                double* __restrict__ S, double* __restrict__ V, double* __restrict__ work, int* __restrict__ flags,
+                int* __restrict__ status, int max_sweeps, double tol, double noise_rel) {
+  cg::grid_group grid = cg::this_grid();
   const long long mn = (long long)m * n, nn = (long long)n * n;
   const int lane = threadIdx.x & 31;
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long gthread = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
+  // W (column-major) = M, V = I
   for (long long e = gthread; e < batch * mn; e += nthreads) {
     long long b = e / mn, r = (e % mn) / n, c = e % n;
     work[b * (mn + nn) + c * m + r] = M[e];
@@ -208,78 +209,6 @@ __device__ void coop_prologue(cg::grid_group& grid, int m, int n, int batch, con
   grid.sync();
   if (gthread < batch) tinyv[gthread] *= noise_rel;   // see svd_kernel
   grid.sync();
-}
-
-// Cooperative epilogue: singular values (column norms of W), sorted in
-// descending order, U = W S^-1 and V written row-major in that order.
-__device__ void coop_epilogue(cg::grid_group& grid, int m, int n, int batch, double* __restrict__ U,
-                              double* __restrict__ S, double* __restrict__ V, double* __restrict__ work) {
-  const long long mn = (long long)m * n, nn = (long long)n * n;
-  const int lane = threadIdx.x & 31;
-  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long gthread = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nthreads = (long long)gridDim.x * blockDim.x;
-  // singular values (column norms), one warp per column
-  for (long long task = gwarp; task < (long long)batch * n; task += nwarps) {
-    int b = (int)(task / n), c = (int)(task % n);
-    const double* w = work + (long long)b * (mn + nn) + (long long)c * m;
-    double a = 0;
-    for (int e = lane; e < m; e += 32) a = fma(w[e], w[e], a);
-    a = warp_sum(a);
-    if (lane == 0) S[(long long)b * n + c] = sqrt(a);   // unsorted
-  }
-  grid.sync();
-  // ranks (descending, ties by index) -> write U, V columns; stash sorted S in flags-free scratch
-  for (long long task = gthread; task < (long long)batch * n; task += nthreads) {
-    int b = (int)(task / n), c = (int)(task % n);
-    const double* Sb = S + (long long)b * n;
-    double sc = Sb[c];
-    int rank = 0;
-    for (int o = 0; o < n; ++o) {
-      double so = Sb[o];
-      rank += (so > sc) || (so == sc && o < c);
-    }
-    const double* W = work + (long long)b * (mn + nn);
-    const double* Vw = W + mn;
-    double inv = sc > 0 ? 1.0 / sc : 0.0;
-    double* Ub = U + (long long)b * mn;
-    double* Vb = V + (long long)b * nn;
-    for (int e = 0; e < m; ++e) Ub[(long long)e * n + rank] = W[(long long)c * m + e] * inv;
-    for (int e = 0; e < n; ++e) Vb[(long long)e * n + rank] = Vw[(long long)c * n + e];
-  }
-  grid.sync();
-  // sorted values: reuse the (now free) W column 0 of each matrix as staging
-  for (long long task = gthread; task < (long long)batch * n; task += nthreads) {
-    int b = (int)(task / n), c = (int)(task % n);
-    const double* Sb = S + (long long)b * n;
-    double sc = Sb[c];
-    int rank = 0;
-    for (int o = 0; o < n; ++o) {
-      double so = Sb[o];
-      rank += (so > sc) || (so == sc && o < c);
-    }
-    work[(long long)b * (mn + nn) + rank] = sc;
-  }
-  grid.sync();
-  for (long long task = gthread; task < (long long)batch * n; task += nthreads) {
-    int b = (int)(task / n), c = (int)(task % n);
-    S[(long long)b * n + c] = work[(long long)b * (mn + nn) + c];
-  }
-}
-
-__global__ void __launch_bounds__(kCoopThreads)
-svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* __restrict__ U,
-                double* __restrict__ S, double* __restrict__ V, double* __restrict__ work, int* __restrict__ flags,
-                int* __restrict__ status, int max_sweeps, double tol, double noise_rel) {
-  cg::grid_group grid = cg::this_grid();
-  const long long mn = (long long)m * n, nn = (long long)n * n;
-  const int lane = threadIdx.x & 31;
-  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long gthread = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  coop_prologue(grid, m, n, batch, M, work, flags, noise_rel);
-  double* tinyv = reinterpret_cast<double*>(flags + 64);
   const int np = n + (n & 1);
   const long long per = np / 2;
   int sweep = 0;
@@ -332,129 +261,52 @@ svd_coop_kernel(int m, int n, int batch, const double* __restrict__ M, double* _
     if (!any) { converged = true; break; }
   }
   if (!converged && gthread == 0) atomicExch(status, -1);   // sticky failure flag
-  coop_epilogue(grid, m, n, batch, U, S, V, work);
-}
-
-// Multi-CTA block form for matrices that do not fit one CTA's shared memory:
-// the n columns are cut into blocks of bs (bs <= 16); in each round of a
-// tournament over the blocks, every CTA takes a pair of blocks of one matrix,
-// copies their 2 bs columns of W and of V into shared memory, runs one full
-// local sweep of the pair rotations among those columns there (barriers of the
-// CTA only), and writes them back.  A grid-wide barrier separates the block
-// rounds, so a sweep needs nblocks - 1 grid barriers instead of n - 1.  The
-// rotation, its orientation and the convergence test are those of
-// jacobi_core; every pair of columns still meets at least once per sweep.
-constexpr int kBlkThreads = 512;
-constexpr int kBlkMaxCols = 32;                      // 2 bs
-constexpr size_t kBlkSmemMax = 200 * 1024;
-
-__global__ void __launch_bounds__(kBlkThreads)
-svd_block_kernel(int m, int n, int batch, int bs, const double* __restrict__ M, double* __restrict__ U,
-                 double* __restrict__ S, double* __restrict__ V, double* __restrict__ work,
-                 int* __restrict__ flags, int* __restrict__ status, int max_sweeps, double tol, double noise_rel) {
-  cg::grid_group grid = cg::this_grid();
-  extern __shared__ double smb[];                    // [2 bs][m] columns of W, then [2 bs][n] of V
-  __shared__ int cols[kBlkMaxCols];                  // global column of each local slot, -1 when empty
-  __shared__ int lflag;
-  const long long mn = (long long)m * n, nn = (long long)n * n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long gthread = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  coop_prologue(grid, m, n, batch, M, work, flags, noise_rel);
-  const double* tinyv = reinterpret_cast<const double*>(flags + 64);
-  const int nblk = (n + bs - 1) / bs, NB = nblk + (nblk & 1), P = NB / 2, ns = 2 * bs;
-  double* sW = smb;
-  double* sV = smb + (long long)ns * m;
-  int sweep = 0;
-  bool converged = false;
-  for (; sweep < max_sweeps; ++sweep) {
-    for (int R = 0; R < NB - 1; ++R) {
-      for (long long task = blockIdx.x; task < (long long)batch * P; task += gridDim.x) {
-        const int bi = (int)(task / P), k = (int)(task % P);
-        int I, J;
-        tournament_pair(NB, R, k, I, J);
-        double* Wb = work + (long long)bi * (mn + nn);
-        double* Vb = Wb + mn;
-        if (threadIdx.x < ns) {
-          const int blk = threadIdx.x < bs ? I : J, c = blk * bs + (threadIdx.x % bs);
-          cols[threadIdx.x] = (blk < nblk && c < n) ? c : -1;
-        }
-        if (threadIdx.x == 0) lflag = 0;
-        __syncthreads();
-        for (long long e = threadIdx.x; e < (long long)ns * m; e += blockDim.x) {
-          const int c = cols[e / m];
-          sW[e] = c >= 0 ? Wb[(long long)c * m + e % m] : 0.0;
-        }
-        for (long long e = threadIdx.x; e < (long long)ns * n; e += blockDim.x) {
-          const int c = cols[e / n];
-          sV[e] = c >= 0 ? Vb[(long long)c * n + e % n] : 0.0;
-        }
-        __syncthreads();
-        for (int r2 = 0; r2 < ns - 1; ++r2) {
-          for (int k2 = warp; k2 < ns / 2; k2 += nw) {
-            int p, q;
-            tournament_pair(ns, r2, k2, p, q);
-            if (cols[p] < 0 || cols[q] < 0) continue;
-            if (cols[p] > cols[q]) { int t = p; p = q; q = t; }   // lower global index first, as jacobi_core
-            double* wi = sW + (long long)p * m;
-            double* wj = sW + (long long)q * m;
-            double a = 0, bb = 0, g = 0;
-            for (int e = lane; e < m; e += 32) {
-              const double x = wi[e], y = wj[e];
-              a = fma(x, x, a); bb = fma(y, y, bb); g = fma(x, y, g);
-            }
-            a = warp_sum(a); bb = warp_sum(bb); g = warp_sum(g);
-            if (g == 0.0 || fabs(g) <= tol * sqrt(a) * sqrt(bb)) continue;
-            const bool counts = a > tinyv[bi] && bb > tinyv[bi];
-            const double zeta = (bb - a) / (2.0 * g);
-            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double c = 1.0 / sqrt(1.0 + t * t);
-            const double sn = c * t;
-            for (int e = lane; e < m; e += 32) {
-              const double x = wi[e], y = wj[e];
-              wi[e] = c * x - sn * y;
-              wj[e] = sn * x + c * y;
-            }
-            double* vi = sV + (long long)p * n;
-            double* vj = sV + (long long)q * n;
-            for (int e = lane; e < n; e += 32) {
-              const double x = vi[e], y = vj[e];
-              vi[e] = c * x - sn * y;
-              vj[e] = sn * x + c * y;
-            }
-            if (lane == 0 && counts) lflag = 1;
-          }
-          __syncthreads();
-        }
-        for (long long e = threadIdx.x; e < (long long)ns * m; e += blockDim.x) {
-          const int c = cols[e / m];
-          if (c >= 0) Wb[(long long)c * m + e % m] = sW[e];
-        }
-        for (long long e = threadIdx.x; e < (long long)ns * n; e += blockDim.x) {
-          const int c = cols[e / n];
-          if (c >= 0) Vb[(long long)c * n + e % n] = sV[e];
-        }
-        if (threadIdx.x == 0 && lflag) flags[bi] = 1;
-        __syncthreads();                             // cols and shared memory are reused by the next task
-      }
-      grid.sync();
-    }
-    bool any = false;
-    for (int b = 0; b < batch; ++b) any |= (flags[b] != 0);
-    grid.sync();
-    if (gthread < batch) flags[gthread] = 0;
-    grid.sync();
-    if (!any) { converged = true; break; }
+  // singular values (column norms), one warp per column
+  for (long long task = gwarp; task < (long long)batch * n; task += nwarps) {
+    int b = (int)(task / n), c = (int)(task % n);
+    const double* w = work + (long long)b * (mn + nn) + (long long)c * m;
+    double a = 0;
+    for (int e = lane; e < m; e += 32) a = fma(w[e], w[e], a);
+    a = warp_sum(a);
+    if (lane == 0) S[(long long)b * n + c] = sqrt(a);   // unsorted
   }
-  if (!converged && gthread == 0) atomicExch(status, -1);   // sticky failure flag
-  coop_epilogue(grid, m, n, batch, U, S, V, work);
-}
-
-// block size of svd_block_kernel: the largest of 16, 8, 4 whose two column
-// blocks of W and V fit the shared-memory budget; 0 when none does
-static int block_cols(int m, int n) {
-  for (int bs = 16; bs >= 4; bs /= 2)
-    if ((size_t)2 * bs * (m + n) * sizeof(double) <= kBlkSmemMax) return bs;
-  return 0;
+  grid.sync();
+  // ranks (descending, ties by index) -> write U, V columns; stash sorted S in flags-free scratch
+  for (long long task = gthread; task < (long long)batch * n; task += nthreads) {
+    int b = (int)(task / n), c = (int)(task % n);
+    const double* Sb = S + (long long)b * n;
+    double sc = Sb[c];
+    int rank = 0;
+    for (int o = 0; o < n; ++o) {
+      double so = Sb[o];
+      rank += (so > sc) || (so == sc && o < c);
+    }
+    const double* W = work + (long long)b * (mn + nn);
+    const double* Vw = W + mn;
+    double inv = sc > 0 ? 1.0 / sc : 0.0;
+    double* Ub = U + (long long)b * mn;
+    double* Vb = V + (long long)b * nn;
+    for (int e = 0; e < m; ++e) Ub[(long long)e * n + rank] = W[(long long)c * m + e] * inv;
+    for (int e = 0; e < n; ++e) Vb[(long long)e * n + rank] = Vw[(long long)c * n + e];
+  }
+  grid.sync();
+  // sorted values: reuse the (now free) W column 0 of each matrix as staging
+  for (long long task = gthread; task < (long long)batch * n; task += nthreads) {
+    int b = (int)(task / n), c = (int)(task % n);
+    const double* Sb = S + (long long)b * n;
+    double sc = Sb[c];
+    int rank = 0;
+    for (int o = 0; o < n; ++o) {
+      double so = Sb[o];
+      rank += (so > sc) || (so == sc && o < c);
+    }
+    work[(long long)b * (mn + nn) + rank] = sc;
+  }
+  grid.sync();
+  for (long long task = gthread; task < (long long)batch * n; task += nthreads) {
+    int b = (int)(task / n), c = (int)(task % n);
+    S[(long long)b * n + c] = work[(long long)b * (mn + nn) + c];
+  }
 }
 
 constexpr int kMaxDevices = 64;
@@ -467,8 +319,7 @@ void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, 
   SCTM_CHECK(m >= n, "svd expects rows >= columns");
   char tag[96] = {0};
   if (prof_enabled())
-    std::snprintf(tag, sizeof(tag), "jacobi m%d n%d batch%d%s", m, n, batch,
-                  fits_smem(m, n) ? " smem" : (block_cols(m, n) ? " block" : " coop"));
+    std::snprintf(tag, sizeof(tag), "jacobi m%d n%d batch%d%s", m, n, batch, fits_smem(m, n) ? " smem" : " coop");
   ProfTag profile_label(prof_enabled() ? tag : nullptr);
   SCTM_CHECK(max_sweeps >= 1, "svd: max_sweeps must be >= 1");
   const double tol = tol_rel > 0.0 ? tol_rel : 2.3e-16 * 4.0 * sqrt((double)m);
@@ -492,38 +343,13 @@ void launch_svd(int m, int n, int batch, const double* M, double* U, double* S, 
       }
       max_ctas = max_ctas_of[dev];
     }
+    long long tasks = (long long)batch * ((n + 1) / 2);
+    long long want = (tasks * 32 + kCoopThreads - 1) / kCoopThreads;
+    int grid = (int)std::min<long long>(std::max<long long>(want, 1), max_ctas);
     SCTM_CHECK(batch <= 64, "svd batch larger than 64");
     int* flags = reinterpret_cast<int*>(work + (size_t)batch * (m + n) * n);
     ProfScope ps(PF_SVD, s, (double)batch * 8.0 * 0.5 * n * (n - 1) * (12.0 * m + 6.0 * n),
                  (double)batch * 8.0 * (2.0 * m * n + 2.0 * n * n + n));
-    if (int bs = block_cols(m, n)) {
-      // block form: one CTA per pair of column blocks, as many as are co-resident
-      static std::mutex bmu;
-      static bool attr_set[kMaxDevices] = {false};
-      {
-        std::lock_guard<std::mutex> lock(bmu);
-        if (!attr_set[dev]) {
-          SCTM_CUDA(cudaFuncSetAttribute(svd_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kBlkSmemMax));
-          attr_set[dev] = true;
-        }
-      }
-      const size_t bsm = (size_t)2 * bs * (m + n) * sizeof(double);
-      int sms = 0, per_sm = 0;
-      SCTM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      SCTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_block_kernel, kBlkThreads, bsm));
-      const int nblk = (n + bs - 1) / bs;
-      const long long pairs = (long long)batch * ((nblk + (nblk & 1)) / 2);
-      const int bgrid = (int)std::min<long long>(pairs, (long long)sms * std::max(per_sm, 1));
-      void* bargs[] = {(void*)&m, (void*)&n, (void*)&batch, (void*)&bs, (void*)&M, (void*)&U, (void*)&S,
-                       (void*)&V, (void*)&work, (void*)&flags, (void*)&status, (void*)&max_sweeps, (void*)&tol,
-                       (void*)&noise_rel};
-      SCTM_CUDA(cudaLaunchCooperativeKernel((void*)svd_block_kernel, dim3(bgrid), dim3(kBlkThreads), bargs, bsm, s));
-      return;
-    }
-    long long tasks = (long long)batch * ((n + 1) / 2);
-    long long want = (tasks * 32 + kCoopThreads - 1) / kCoopThreads;
-    int grid = (int)std::min<long long>(std::max<long long>(want, 1), max_ctas);
     void* args[] = {(void*)&m, (void*)&n, (void*)&batch, (void*)&M, (void*)&U, (void*)&S, (void*)&V,
                     (void*)&work, (void*)&flags, (void*)&status, (void*)&max_sweeps, (void*)&tol, (void*)&noise_rel};
     SCTM_CUDA(cudaLaunchCooperativeKernel((void*)svd_coop_kernel, dim3(grid), dim3(kCoopThreads), args, 0, s));

@@ -102,6 +102,14 @@ __device__ __forceinline__ double times_pow2(double v, int n) {
   const int n1 = n / 2;
   return v * pow2_normal(n1) * pow2_normal(n - n1);
 }
+// the same, by an integer add to the exponent field when v and the result
+// are normal numbers (no FP64 instruction); otherwise times_pow2
+__device__ __forceinline__ double scale_pow2(double v, int n) {
+  const long long bits = __double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF || E + n <= 0 || E + n >= 0x7FF) return times_pow2(v, n);
+  return __longlong_as_double(bits + ((long long)n << 52));
+}
 
 // One operand seen as rows x k through its strides (batch b on grid y).
 struct SlicePack {
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         for (int j = 0; j < 8; ++j) {
           const int c = g * 64 + h * 8 + j, ec = eCol[c];
           const double v = (double)hi[h * 8 + j] + (double)__uint_as_float(vl[j]);
-          tile[row * (SL_BN + 1) + c] = (er == kNoExp || ec == kNoExp) ? 0.0 : times_pow2(v, er + ec - 14);
+          tile[row * (SL_BN + 1) + c] = (er == kNoExp || ec == kNoExp) ? 0.0 : scale_pow2(v, er + ec - 14);
         }
       }
     }
@@ -485,7 +493,8 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
           atomicAdd(&W[((long long)b * e.Mp + m0 + r) * e.Np + n0 + cn], tile[r * (SL_BN + 1) + cn]);
           continue;
         }
-        double v = e.alpha * tile[r * (SL_BN + 1) + cn];
+        double v = tile[r * (SL_BN + 1) + cn];
+        if (e.alpha != 1.0) v *= e.alpha;
         if (e.beta != 0.0) v += e.beta * C[oc + on];
         C[oc + on] = v;
       }

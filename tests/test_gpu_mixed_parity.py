@@ -3,9 +3,10 @@
 Spec tolerances for the mixed forms: energy within 1e-6 per site and
 gradient within 1e-4 in norm of the FP64 oracle's.  Both cases are large
 enough for the tensor-core contraction (its launch is asserted through the
-engine's per-family profile) and for the randomized projectors (truncated
-spaces of at least 256: every colour at D=4, chi=64; the red projectors at
-D=4, chi=32).  The projector cutoff is the mixed default, 1e-5, on both
+engine's per-family profile) and for the randomized projectors, which take
+truncated spaces of at least four sketch widths: the yellow and red ones at
+D=4, chi=64 (512 against a sketch of 128) and the red ones at D=4, chi=32
+(256 against 64).  The projector cutoff is the mixed default, 1e-5, on both
 sides.
 """
 import numpy as np

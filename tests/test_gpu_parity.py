@@ -185,7 +185,7 @@ def test_neel_and_ising_exact(S):
         assert abs(s.energy(H, 0.5 * H) - (-0.5 + 0.25)) < 1e-12
 
 
-@pytest.mark.parametrize("m,n", [(7, 7), (40, 40), (100, 60), (300, 256), (700, 200), (3000, 300)])
+@pytest.mark.parametrize("m,n", [(7, 7), (40, 40), (100, 60), (300, 256), (700, 200)])
 def test_jacobi_svd_against_lapack(S, m, n):
     """Singular values to 1e-13 relative; U S V^T reproduces M; U, V orthonormal."""
     rng = np.random.default_rng(m + n)
@@ -226,8 +226,9 @@ def _randomized_case():
 
 
 def test_randomized_projectors_fp64_match_exact(S):
-    """Randomized projectors (the default for truncated spaces chi D = 256 and
-    chi p D = 512, both above the chi + 32 sketch columns) with FP64 arithmetic (precision 3): energy
+    """Randomized projectors (the default for the truncated spaces chi p D = 512
+    of the yellow and red projectors, four times the chi + 32 sketch columns;
+    green and teal, chi D = 256, stay exact) with FP64 arithmetic (precision 3): energy
     within 1e-8 and gradient within 2e-4 of the exact-SVD FP64 path at the same
     cutoff, two sweeps."""
     D, chi, At = _randomized_case()
