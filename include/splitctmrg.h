@@ -192,30 +192,35 @@ SCTM_API int energy_grad_host(sctm_handle h, const double* A_cell_host, int swee
                      const double* h_diag_host, double* e_per_site, double* grad_host);
 
 /* Energy per site at the converged environment and its gradient by implicit
- * differentiation of the fixed point env* = f(env*, A), f one full step of
- * the four directional moves.  Sec. II.B iterates f until the environment
- * converges and Sec. I / Sec. III differentiate the converged energy; the rule
- * follows from the implicit function theorem:
- *   dE/dA = dE/dA|env* + x^T df/dA|env*,  x = dE/denv* + x^T df/denv|env*.
+ * differentiation of the fixed point env* = F(env*, A).  Sec. II.B iterates
+ * full steps f (the four directional moves) until the environment converges,
+ * and Sec. I / Sec. III differentiate the converged energy.  The rule follows
+ * from the implicit function theorem:
+ *   dE/dA = dE/dA|env* + x^T dF/dA|env*,  x = dE/denv* + x^T dF/denv|env*.
+ * F is f applied p times, p the smallest number of steps (at most max_period;
+ * <= 0: 4) after which no entry of any environment tensor has moved by more
+ * than fixed_point_tol of that tensor's largest entry.  At converged spectra
+ * the signs of the sign-fixed projectors, and with them rows of the
+ * environment tensors, can still cycle from step to step; p closes the cycle.
  * Steps: initial environment, full steps until the corner spectra change by
- * less than tol (as split_ctmrg_run) or max_sweeps; one more step must change
- * no entry of any environment tensor by more than fixed_point_tol of that
- * tensor's largest entry, else SCTM_ERR_NOT_FIXED_POINT (the projector gauge
- * is not fixed from step to step); the energy's reverse pass at env*; x by
- * iterating its equation from x = dE/denv* until the change is below
- * solve_tol of |x|, at most max_iter times, else
- * SCTM_ERR_NO_CONVERGENCE; each iteration is one reverse pass through the
- * step (its four moves recomputed from checkpoints, decompositions reused).
+ * less than tol (as split_ctmrg_run) or max_sweeps; the period search
+ * (SCTM_ERR_NOT_FIXED_POINT when there is none); the energy's reverse pass at
+ * env*; x by iterating its equation from x = dE/denv* until the change is below
+ * solve_tol of |x|, at most max_iter times, else SCTM_ERR_NO_CONVERGENCE.  Each
+ * iteration is one reverse pass through the 4p moves of F, recomputed from
+ * checkpoints with the decompositions reused.
  * Tolerances <= 0 take the defaults: tol 1e-13, fixed_point_tol 1e-9,
  * solve_tol 1e-12 at precisions 0 and 3; 1e-7, 1e-5, 1e-6 in the precisions
  * with FP32-level contractions (1, 2, 4).
  * grad_dev (device, layout of A_cell) receives dE/dA.  Optional host outputs:
- * sweeps_done, solver_iterations, fixed_point_change (the largest relative
- * change of that extra step).  Leaves env* in the handle; synchronises. */
+ * sweeps_done, period_out (p), solver_iterations, fixed_point_change (the
+ * largest relative change after the last step tried).  Leaves env* in the
+ * handle; synchronises. */
 SCTM_API int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps, double tol,
                                   const double* h_nn_host, const double* h_diag_host, double fixed_point_tol,
-                                  double solve_tol, int max_iter, double* e_per_site, double* grad_dev,
-                                  int* sweeps_done, int* solver_iterations, double* fixed_point_change);
+                                  double solve_tol, int max_iter, int max_period, double* e_per_site,
+                                  double* grad_dev, int* sweeps_done, int* period_out, int* solver_iterations,
+                                  double* fixed_point_change);
 
 /* Environment of site (x, y) (the split environment of Fig. 2, Sec. II.B; for
  * the conventional algorithm the environment of Fig. 1, Sec. II.A) into

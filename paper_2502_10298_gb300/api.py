@@ -63,7 +63,7 @@ def load_library(path: str = LIB_PATH):
         "energy_2x2": (i, [vp, _dp, _dp, _dp]),
         "energy_grad": (i, [vp, vp, i, _dp, _dp, _dp, vp]),
         "energy_grad_host": (i, [vp, _dp, i, _dp, _dp, _dp, _dp]),
-        "energy_grad_implicit": (i, [vp, vp, i, d, _dp, _dp, d, d, i, _dp, vp, _ip, _ip, _dp]),
+        "energy_grad_implicit": (i, [vp, vp, i, d, _dp, _dp, d, d, i, i, _dp, vp, _ip, _ip, _ip, _dp]),
         "sctm_get_env": (i, [vp, i, i, vp]),
         "sctm_workspace_high_water": (i, [vp, ctypes.POINTER(ctypes.c_size_t)]),
         "sctm_profile": (i, [vp, i, _dp]),
@@ -179,19 +179,22 @@ def energy_grad_host(h, A_cell: np.ndarray, sweeps: int, h_nn, h_diag=None, grad
 
 
 def energy_grad_implicit(h, A_cell: torch.Tensor, h_nn, h_diag=None, max_sweeps: int = 300, tol: float = 0.0,
-                         fixed_point_tol: float = 0.0, solve_tol: float = 0.0, max_iter: int = 500):
-    """(E, grad, info) by implicit differentiation of the converged environment;
-    info = dict(sweeps, solver_iterations, fixed_point_change).  Zero tolerances
-    take the library defaults."""
+                         fixed_point_tol: float = 0.0, solve_tol: float = 0.0, max_iter: int = 500,
+                         max_period: int = 4):
+    """(E, grad, info) by implicit differentiation of the converged environment
+    as a fixed point of `period` full steps; info = dict(sweeps, period,
+    solver_iterations, fixed_point_change).  Zero tolerances take the library
+    defaults."""
     a, pa = _hp(h_nn)
     b, pb = _hp(h_diag)
     g = torch.empty_like(A_cell)
     e = ctypes.c_double()
-    n, it, fp = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    n, per, it, fp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(h, _lib.energy_grad_implicit(h, _dev(A_cell), int(max_sweeps), float(tol), pa, pb, float(fixed_point_tol),
-                                        float(solve_tol), int(max_iter), ctypes.byref(e), _dev(g), ctypes.byref(n),
-                                        ctypes.byref(it), ctypes.byref(fp)))
-    return e.value, g, {"sweeps": n.value, "solver_iterations": it.value, "fixed_point_change": fp.value}
+                                        float(solve_tol), int(max_iter), int(max_period), ctypes.byref(e), _dev(g),
+                                        ctypes.byref(n), ctypes.byref(per), ctypes.byref(it), ctypes.byref(fp)))
+    return e.value, g, {"sweeps": n.value, "period": per.value, "solver_iterations": it.value,
+                        "fixed_point_change": fp.value}
 
 
 def sctm_get_env(h, x, y, chi, D, conventional=False, chi_I=None):

@@ -735,11 +735,13 @@ int energy_grad_host(sctm_handle h, const double* A_cell_host, int sweeps, const
 
 int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps, double tol,
                          const double* h_nn_host, const double* h_diag_host, double fixed_point_tol,
-                         double solve_tol, int max_iter, double* e_per_site, double* grad_dev, int* sweeps_done,
-                         int* solver_iterations, double* fixed_point_change) {
+                         double solve_tol, int max_iter, int max_period, double* e_per_site, double* grad_dev,
+                         int* sweeps_done, int* period_out, int* solver_iterations, double* fixed_point_change) {
   return guard(h, [&]() {
     SCTM_CHECK(A_cell_dev && h_nn_host && e_per_site && grad_dev, "null argument");
     SCTM_CHECK(max_sweeps >= 0 && max_iter >= 1, "max_sweeps must be >= 0 and max_iter >= 1");
+    if (max_period <= 0) max_period = 4;
+    SCTM_CHECK(max_period <= 16, "max_period must be at most 16");
     // defaults: FP64 as the rule's own tolerances; the mixed precisions carry
     // FP32-level rounding in the networks, which sets the floor of the
     // spectral change, of the step-to-step change and of the adjoint iterate
@@ -766,51 +768,64 @@ int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps
     int n = 0;
     run_to_tol(h, max_sweeps, tol, &n, nullptr);
     if (sweeps_done) *sweeps_done = n;
-    // 2. one more step f(env*) from checkpoints ck[0] = env* .. ck[4] = f(env*),
-    // keeping the decompositions of its moves for the taped recomputations
-    double* ck = c.arena.alloc(nE * 5);
+    // 2. the p-step map F = f^p: steps from env* with checkpoints ck[0] = env*,
+    // ck[m] after move m, keeping the decompositions of every move for the taped
+    // recomputations; p is the smallest number of steps (<= max_period) after
+    // which no entry of any environment tensor has moved by more than
+    // fixed_point_tol of that tensor's largest entry (the signs of the
+    // projectors, and with them rows of the environment, may cycle at
+    // converged spectra)
+    const int max_moves = 4 * max_period;
+    double* ck = c.arena.alloc(nE * (max_moves + 1));
     double* gE = c.arena.alloc(nE);     // dE/denv*
     double* x = c.arena.alloc(nE);      // adjoint iterate
     double* xn = c.arena.alloc(nE);
     double* gbuf = c.arena.alloc(nE);
     double* gA0 = c.arena.alloc(nA);    // dE/dA at fixed env*
-    double* red = c.arena.alloc(2 * N * NKEY + 4);
+    const long long ntens = N * NKEY;
+    double* red = c.arena.alloc(2 * ntens + 4);
     save_env(h, ck);
     bind_store(h, ck);
     const size_t top = c.arena.mark();
-    std::vector<std::vector<std::array<Tensor, 3>>> decomp(4);
-    for (int mv = 0; mv < 4; ++mv) {
-      c.decomp = Ctx::DecompCache();
-      c.decomp.mode = 1;
-      move(c, P, h->cell, mv);
-      decomp[mv] = std::move(c.decomp.entries);
-      c.decomp = Ctx::DecompCache();
-      save_env(h, ck + (mv + 1) * nE);
-      bind_store(h, ck + (mv + 1) * nE);
-      c.arena.release(top);
-    }
-    check_svd(h);
-    // element-wise fixed point: max over tensors of max|f(env*) - env*| / max|env*|
-    {
+    std::vector<std::vector<std::array<Tensor, 3>>> decomp(max_moves);
+    int period = 0;
+    double worst = 0.0;
+    std::vector<double> hr(2 * ntens);
+    for (int q = 1; q <= max_period && !period; ++q) {
+      for (int d = 0; d < 4; ++d) {
+        const int mv = 4 * (q - 1) + d;
+        c.decomp = Ctx::DecompCache();
+        c.decomp.mode = 1;
+        move(c, P, h->cell, d);
+        decomp[mv] = std::move(c.decomp.entries);
+        c.decomp = Ctx::DecompCache();
+        save_env(h, ck + (mv + 1) * nE);
+        bind_store(h, ck + (mv + 1) * nE);
+        c.arena.release(top);
+      }
+      check_svd(h);
+      // element-wise change after q steps: max over tensors of max|F(env*) - env*| / max|env*|
       long long i = 0;
       for (int xx = 0; xx < P.Lx; ++xx)
         for (int yy = 0; yy < P.Ly; ++yy)
           for (int k = 0; k < NKEY; ++k, ++i) {
-            const Tensor a = key_view(h, ck, xx, yy, k), b = key_view(h, ck + 4 * nE, xx, yy, k);
-            launch_maxabs_pair(a.numel(), b.data, a.data, red + 2 * i, c.stream);
+            const Tensor a0 = key_view(h, ck, xx, yy, k), b0 = key_view(h, ck + 4 * q * nE, xx, yy, k);
+            launch_maxabs_pair(a0.numel(), b0.data, a0.data, red + 2 * i, c.stream);
           }
-      std::vector<double> hr(2 * i);
       SCTM_CUDA(cudaMemcpyAsync(hr.data(), red, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
       SCTM_CUDA(cudaStreamSynchronize(c.stream));
-      double worst = 0.0;
-      for (long long j = 0; j < i; ++j)
+      worst = 0.0;
+      for (long long j = 0; j < ntens; ++j)
         if (hr[2 * j + 1] > 0) worst = std::max(worst, hr[2 * j] / hr[2 * j + 1]);
-      if (fixed_point_change) *fixed_point_change = worst;
-      if (!(worst <= fixed_point_tol))
-        throw CodedError(SCTM_ERR_NOT_FIXED_POINT,
-                         "environment is not an element-wise fixed point (relative change " + std::to_string(worst) +
-                             "): the projector gauge is not fixed between steps");
+      if (worst <= fixed_point_tol) period = q;
     }
+    if (fixed_point_change) *fixed_point_change = worst;
+    if (period_out) *period_out = period;
+    if (!period)
+      throw CodedError(SCTM_ERR_NOT_FIXED_POINT,
+                       "environment is not an element-wise fixed point of up to " + std::to_string(max_period) +
+                           " steps (relative change " + std::to_string(worst) + ")");
+    const int nmoves = 4 * period;
     // 3. energy at env*, taped: dE/denv* and dE/dA
     bind_A(h, true);
     SCTM_CUDA(cudaMemsetAsync(h->Agrad, 0, nA * sizeof(double), c.stream));
@@ -821,11 +836,11 @@ int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps
     c.tape.active = false;
     c.arena.release(top);
     SCTM_CUDA(cudaMemcpyAsync(gA0, h->Agrad, nA * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-    // out = x^T df/denv through the four moves of the step, each recomputed
-    // taped from its checkpoint (x^T df/dA accumulates into the A gradient)
+    // out = x^T dF/denv through the moves of F, each recomputed taped from its
+    // checkpoint (x^T dF/dA accumulates into the A gradient)
     auto vjp = [&](const double* xin, double* out) {
       SCTM_CUDA(cudaMemcpyAsync(gbuf, xin, nE * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-      for (int mv = 3; mv >= 0; --mv) {
+      for (int mv = nmoves - 1; mv >= 0; --mv) {
         c.tape.active = true;
         bind_leaves(h, ck + mv * nE);
         std::vector<SiteEnv> leaves = h->cell.env;
@@ -833,7 +848,7 @@ int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps
         c.decomp = Ctx::DecompCache();
         c.decomp.mode = 2;
         c.decomp.entries = decomp[mv];
-        move(c, P, h->cell, mv);
+        move(c, P, h->cell, mv % 4);
         SCTM_CHECK(c.decomp.next == c.decomp.entries.size(), "decomposition cache: entries left over");
         c.decomp = Ctx::DecompCache();
         seed_env_grad(h, gbuf);
@@ -845,14 +860,14 @@ int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps
       }
       SCTM_CUDA(cudaMemcpyAsync(out, gbuf, nE * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     };
-    // 4. x = dE/denv* + x^T df/denv, iterated from x = dE/denv*
+    // 4. x = dE/denv* + x^T dF/denv, iterated from x = dE/denv*
     SCTM_CUDA(cudaMemcpyAsync(x, gE, nE * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     int it = 0;
     bool converged = false;
     while (it < max_iter && !converged) {
       ++it;
       vjp(x, xn);
-      launch_axpy(nE, 1.0, gE, xn, c.stream);                       // xn = dE/denv* + x^T df/denv
+      launch_axpy(nE, 1.0, gE, xn, c.stream);                       // xn = dE/denv* + x^T dF/denv
       launch_axpy(nE, -1.0, xn, x, c.stream);                       // x <- x - xn (the change)
       launch_dot(1, nE, x, x, 0, red, c.partial, c.stream);
       launch_dot(1, nE, xn, xn, 0, red + 1, c.partial, c.stream);
@@ -866,7 +881,7 @@ int energy_grad_implicit(sctm_handle h, const double* A_cell_dev, int max_sweeps
     if (solver_iterations) *solver_iterations = it;
     if (!converged) throw CodedError(SCTM_ERR_NO_CONVERGENCE, "adjoint fixed-point iteration did not converge");
     check_svd(h);
-    // 5. grad = dE/dA + x^T df/dA
+    // 5. grad = dE/dA + x^T dF/dA
     SCTM_CUDA(cudaMemsetAsync(h->Agrad, 0, nA * sizeof(double), c.stream));
     vjp(x, xn);
     launch_axpy(nA, 1.0, gA0, h->Agrad, c.stream);

@@ -397,7 +397,13 @@ std::vector<SVDResult> svd_many(Ctx& c, const std::vector<Tensor>& Ms, double ep
   double* work = nullptr;
   size_t wn = svd_work_doubles(m, n, nb);
   if (wn) work = c.arena.alloc((long long)wn);
-  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 0.0, 0.0, c.svd_max_sweeps);
+  // columns with norm below 1e-14 of ||M||_F (rounding level, far under any
+  // projector cutoff) are still rotated but do not hold back convergence: the
+  // rotations elsewhere keep refreshing their rounding, so counting them only
+  // runs sweeps to the limit on the rank-deficient halves of a truncated
+  // environment
+  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 1e-28, 0.0,
+             c.svd_max_sweeps);
   if (!tap) c.arena.release(mk);  // later work is stream-ordered after the kernel
   for (int i = 0; i < nb; ++i) {
     out[i] = SVDResult{Ub.sub(0, i), Sb.sub(0, i), Vb.sub(0, i)};

@@ -319,11 +319,34 @@ def test_implicit_gradient_matches_unrolled_and_finite_differences():
 
 
 def test_implicit_gradient_refuses_a_gauge_that_is_not_fixed():
-    """The conventional scheme's tensors flip signs between steps even when its
-    corner spectra have converged; the fixed-point rule does not apply there."""
+    """The conventional scheme's tensors keep changing sign between steps even
+    when its corner spectra have converged, with no short period: the
+    fixed-point rule does not apply there."""
     A = _near_product(1, 1, 2, 0.25, seed=5)
     with pytest.raises(ValueError):
         implicit_energy_grad(A, 8, HR, split=False, max_sweeps=40)
+
+
+@pytest.mark.parametrize("seed,period", [(0, 2), (3, None)])
+def test_implicit_gradient_through_a_sign_cycle(seed, period):
+    """A random D=2 state: at converged spectra the projector signs cycle, so
+    the environment is a fixed point of a few steps only.  The rule applied to
+    that p-step map must still give the derivative of the converged energy
+    (central difference along a random direction, 1e-6) and report its period."""
+    A = I.random_cell(1, 1, 2, 2, seed=seed)
+    chi = 8
+    E, g, info = implicit_energy_grad(A, chi, H)
+    if period is not None:
+        assert info["period"] == period
+    v = np.random.default_rng(7).standard_normal(A.shape)
+    v /= np.linalg.norm(v)
+    eps = 1e-5
+
+    def converged(X):
+        env, _, _ = C.ctmrg_run(X, chi, 1e-14, 400)
+        return float(En.energy_per_site(C.as_cell(X), env, H))
+    fd = (converged(A + eps * v) - converged(A - eps * v)) / (2 * eps)
+    assert abs(fd - float((g.numpy() * v).sum())) < 1e-6 * max(abs(fd), 1e-3)
 
 
 def test_honeycomb_bond_closed_forms():
