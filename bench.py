@@ -353,6 +353,8 @@ def main():
     ap.add_argument("--implicit", action="store_true",
                     help="the implicit fixed-point gradient of the converged environment beside the checkpointed "
                          "one (same precision): time, sweeps, solver iterations and peak workspace of each")
+    ap.add_argument("--max-sweeps", type=int, default=60, help="--implicit: sweep limit of the run to convergence")
+    ap.add_argument("--max-iter", type=int, default=60, help="--implicit: iteration limit of the adjoint solve")
     ap.add_argument("--near-product", type=float, default=None,
                     help="--implicit: replace the workload's tensors by a near-product state of the same shape "
                          "(0.8|0> + 0.6|1> on the zero bond index plus this much N(0,1) noise, seed 5)")
@@ -613,7 +615,8 @@ def run_implicit(args):
     g_imp = None
     with S.SplitCTMRG(c["Lx"], c["Ly"], c["p"], c["D"], c["chi"], precision=prec, workspace_bytes=ws) as s:
         try:
-            (e, g_imp, info), sec = timed(lambda: s.energy_grad_implicit(At, h_nn, h_diag, max_sweeps=300))
+            (e, g_imp, info), sec = timed(lambda: s.energy_grad_implicit(At, h_nn, h_diag, max_sweeps=args.max_sweeps,
+                                                                         max_iter=args.max_iter))
             out["implicit"] = {"seconds": sec, "energy_per_site": e, **info,
                                "workspace_high_water_bytes": S.sctm_workspace_high_water(s.h)}
         except S.SctmError as ex:

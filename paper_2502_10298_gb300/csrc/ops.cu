@@ -397,12 +397,10 @@ std::vector<SVDResult> svd_many(Ctx& c, const std::vector<Tensor>& Ms, double ep
   double* work = nullptr;
   size_t wn = svd_work_doubles(m, n, nb);
   if (wn) work = c.arena.alloc((long long)wn);
-  // columns with norm below 1e-14 of ||M||_F (rounding level, far under any
-  // projector cutoff) are still rotated but do not hold back convergence: the
-  // rotations elsewhere keep refreshing their rounding, so counting them only
-  // runs sweeps to the limit on the rank-deficient halves of a truncated
-  // environment
-  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 1e-28, 0.0,
+  // every column counts for convergence: the reverse pass couples the kept
+  // triplets to the rest of the spectrum through the U columns of the
+  // smallest singular values, which must come out orthonormal too
+  launch_svd(m, n, nb, Mb.data, Ub.data, Sb.data, Vb.data, work, c.svd_status, c.stream, 0.0, 0.0,
              c.svd_max_sweeps);
   if (!tap) c.arena.release(mk);  // later work is stream-ordered after the kernel
   for (int i = 0; i < nb; ++i) {
