@@ -1,9 +1,10 @@
 """Implicit (fixed-point) energy gradient on the GPU against the oracle's rule.
 
-The oracle's ``implicit_energy_grad`` converges the environment, checks that
-one more full step is an element-wise fixed point, differentiates the energy
-there and solves the adjoint fixed-point equation (Sec. I, Sec. II.B,
-Sec. III; implicit function theorem).  The engine's ``energy_grad_implicit``
+The oracle's ``implicit_energy_grad`` converges the environment, finds the
+smallest number of full steps (up to four) after which it is an element-wise
+fixed point, differentiates the energy there and solves the adjoint
+fixed-point equation of that many steps (Sec. I, Sec. II.B, Sec. III;
+implicit function theorem).  The engine's ``energy_grad_implicit``
 takes the same steps in FP64.  Cases: near-product states, which the sign-
 fixed projectors bring to an element-wise fixed point of one step, and states
 whose projector signs still cycle at converged spectra, which are fixed points
