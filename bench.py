@@ -318,7 +318,8 @@ def _cpu_args(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1,
+                    help="timed evaluations (one evaluation of the default workload takes about 48 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="d8_chi128_2x2_j1j2", choices=sorted(I.WORKLOADS))
