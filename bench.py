@@ -29,7 +29,7 @@ import ipeps_inputs as I  # noqa: E402
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal (about 152 SMs x 2.07 GHz x 4 flop/clk/SM)
 TC_CORNER_DRAM_BYTES = 6.576915e9 + 0.52181376e9   # ncu, tc_gemm_kernel on one 8192^3 product
-SLICE_CORNER_DRAM_BYTES = 6.670281e9 + 0.521873e9  # ncu, slice_gemm_kernel on one 8192^3 product
+SLICE_CORNER_DRAM_BYTES = 6.583486e9 + 0.520848e9  # ncu, slice_gemm_kernel on one 8192^3 product
 
 
 def load_peaks():
